@@ -1,0 +1,154 @@
+"""Radsort oracle -- TEST INFRASTRUCTURE ONLY.
+
+Python marshalling around ``radsort_oracle.c``, the plain single-threaded CPU
+restatement of the paper's Alg. 1 (out-of-place LSD round) and of the Radsort
+block algorithm (Alg. 2-7, with the parallel-chunk variant of Sec. 4.3).  Only
+``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline leg may
+import this package; the CUDA library never does, and the two share no code.
+
+Every function is pinned in ``tests/test_oracle_pins.py`` to numpy's stable
+argsort, to brute-force stable sorting over exhaustive tiny inputs, and to the
+paper's data invariant (Sec. 2.2) and Lemmas 1-2; planted mistakes
+(``ORACLE_MUTANT``) show that the pins catch them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "radsort_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+
+ERRORS = {
+    0: "ok",
+    -1: "bad argument",
+    -2: "out of memory",
+    -10: "Lemma 1 violated (i_out >= i_in at newBucketBlock)",
+    -11: "Lemma 2 violated (fewer than H unallocated blocks after sortPhase)",
+    -12: "invariant 1 violated (pi is not a permutation)",
+    -13: "invariant 2 violated (P not ascending / out of range)",
+    -14: "invariant 3 violated (block f-1 is not partial)",
+    -15: "invariant 5 violated (element count)",
+    -16: "Finalize wrote a wrong element count",
+    -17: "Finalize exceeded the block-copy bound of Sec. 3",
+}
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n_pi", ctypes.c_uint64),
+        ("head", ctypes.c_uint64),
+        ("t_blocks", ctypes.c_uint64),
+        ("lemma1_checks", ctypes.c_uint64),
+        ("min_unallocated", ctypes.c_uint64),
+        ("fin_copies_main", ctypes.c_uint64),
+        ("fin_copies_rest", ctypes.c_uint64),
+        ("fin_pushes", ctypes.c_uint64),
+        ("extra_bytes", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+def build(mutant: int = 0, force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, -O2); returns the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    so = os.path.join(_BUILD, f"libradsort_oracle_m{mutant}.so")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", f"-DORACLE_MUTANT={mutant}",
+             "-o", tmp, _SRC])
+        os.replace(tmp, so)
+    return so
+
+
+_libs: dict[int, ctypes.CDLL] = {}
+
+
+def _lib(mutant: int = 0) -> ctypes.CDLL:
+    if mutant not in _libs:
+        lib = ctypes.CDLL(build(mutant))
+        P = ctypes.c_void_p
+        lib.ora_lsd_oop.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.c_int, ctypes.c_int]
+        lib.ora_lsd_oop.restype = ctypes.c_int
+        lib.ora_radsort.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.c_int, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int,
+                                    ctypes.c_int, P, P, ctypes.c_uint64, ctypes.POINTER(Stats)]
+        lib.ora_radsort.restype = ctypes.c_int
+        lib.ora_f32_to_ordered.argtypes = [P, ctypes.c_size_t]
+        lib.ora_ordered_to_f32.argtypes = [P, ctypes.c_size_t]
+        lib.ora_mutant_id.restype = ctypes.c_int
+        _libs[mutant] = lib
+    return _libs[mutant]
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise OracleError(ERRORS.get(rc, f"oracle error {rc}"))
+
+
+def _prep(keys, vals):
+    k = np.ascontiguousarray(keys).astype(np.uint64, copy=True)
+    v = None if vals is None else np.ascontiguousarray(vals).astype(np.uint32, copy=True)
+    return k, v
+
+
+def digits_for(key_bits: int, digit_bits: int) -> int:
+    """n_t = ceil(key_bits / digit_bits) (reading G8)."""
+    return -(-key_bits // digit_bits)
+
+
+def lsd_oop(keys, vals=None, *, n_t, sigma, bits, rounds=None, mutant=0):
+    """Alg. 1 applied for `rounds` rounds (default n_t). Returns (keys, vals)."""
+    k, v = _prep(keys, vals)
+    _check(_lib(mutant).ora_lsd_oop(_ptr(k), _ptr(v), k.size, n_t, sigma, bits,
+                                    n_t if rounds is None else rounds))
+    return k, v
+
+
+def radsort(keys, vals=None, *, n_t, sigma, bits, b, p=1, rounds=None, finalize=True,
+            elem_bytes=8, mutant=0, with_stats=False):
+    """Alg. 2 with `p` chunks.  finalize=True: the sorted (keys, vals).
+    finalize=False: the logical sequence after `rounds` rounds."""
+    k, v = _prep(keys, vals)
+    st = Stats()
+    r = n_t if rounds is None else rounds
+    if finalize:
+        rc = _lib(mutant).ora_radsort(_ptr(k), _ptr(v), k.size, n_t, sigma, bits, b, p, r, 1,
+                                      None, None, elem_bytes, ctypes.byref(st))
+        _check(rc)
+        out = (k, v)
+    else:
+        sk = np.zeros(k.size, np.uint64)
+        sv = None if v is None else np.zeros(k.size, np.uint32)
+        rc = _lib(mutant).ora_radsort(_ptr(k), _ptr(v), k.size, n_t, sigma, bits, b, p, r, 0,
+                                      _ptr(sk), _ptr(sv), elem_bytes, ctypes.byref(st))
+        _check(rc)
+        out = (sk, sv)
+    return (out, st.as_dict()) if with_stats else out
+
+
+def f32_to_ordered(u32):
+    a = np.ascontiguousarray(u32).astype(np.uint32, copy=True)
+    _lib().ora_f32_to_ordered(_ptr(a), a.size)
+    return a
+
+
+def ordered_to_f32(u32):
+    a = np.ascontiguousarray(u32).astype(np.uint32, copy=True)
+    _lib().ora_ordered_to_f32(_ptr(a), a.size)
+    return a

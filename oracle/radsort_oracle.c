@@ -1,0 +1,620 @@
+/*
+ * Radsort oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU restatement of the algorithms of
+ * "Parallel O(sqrt n) Overhead LSD Radix Sort" (Clausecker & Schintke):
+ *
+ *   ora_lsd_oop   -- Alg. 1 (out-of-place LSD round), applied for
+ *                    t = n_t-1 ... 0 with a ping-pong buffer.
+ *   ora_radsort   -- Alg. 2 (driver): Alg. 4 (setup), Alg. 5 (sortPhase,
+ *                    newBucketBlock), Alg. 3 (sizeOfNextBlock), Alg. 6
+ *                    (fixupPhase), Alg. 7 (swap/finalize), with the data
+ *                    invariant of Sec. 2.2 and Lemmas 1 and 2 asserted.
+ *                    p > 1 is the parallel variant of Sec. 4.3: the
+ *                    logical blocks are split into p chunks, each with its
+ *                    own head start of sigma blocks (T = 2*sigma*p blocks),
+ *                    its own bucket array B, and one P entry per
+ *                    (bucket, chunk) after the fixup.  p = 1 is exactly the
+ *                    sequential algorithm of Sec. 2.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg
+ * may load this library.  It shares no code with the CUDA path.
+ *
+ * Readings of passages that are garbled or ambiguous in the paper:
+ *   G1 Alg. 3 compares pi[i] with P's entry, but P holds logical indices
+ *      (Sec. 2.1): we compare i itself, and return the length read before
+ *      i_P is advanced.
+ *   G2 Alg. 7 sets j_out from i_in - sigma, which would address T; the text
+ *      puts the data at physical blocks 2*sigma.. : j_out = i_in + H where H
+ *      is the head-start size (sigma for p = 1), i.e. A block i_in - H.
+ *   G3 Alg. 7's swap also exchanges the caller's variables; we keep the loop
+ *      counter apart and track (i_free, j_free) as the text describes.
+ *   G4 "up to b partial blocks described by B" (Sec. 2.3.2) means one per
+ *      bucket: sigma (sigma*p with chunks).
+ *   G5 setup uses floor(n/b)+1 data blocks with the tail always a partial
+ *      block (possibly of length 0), as Alg. 4 does.
+ *   G6 a pull whose source and target overlap is a memmove.
+ *   G8 digit t (t = 0 most significant) of an unsigned key with d-bit digits
+ *      covers bits [(n_t-1-t)d, (n_t-t)d); sigma = 2^d for every digit.
+ *   G7 Lemma 1's i_in is the "next input block" of the variable table: once
+ *      the last element of the current block has been copied, that block
+ *      counts as consumed (read as the loop variable of Alg. 5, the bound
+ *      fails by one at block ends, e.g. b = 1).
+ *   G9 T and unallocated blocks are poisoned (0xA5 bytes) so that a read of
+ *      unallocated data shows up in the output.
+ *
+ * Function pins (tests/test_oracle_pins.py): every function here is pinned
+ * to numpy's stable argsort, to brute-force stable sorting of exhaustive
+ * tiny inputs, and to the invariants and lemmas of the paper.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0 /* >0 plants a known mistake (used by the pin tests) */
+#endif
+
+/* error codes (negative) */
+#define ORA_OK 0
+#define ORA_EARG -1
+#define ORA_ENOMEM -2
+#define ORA_LEMMA1 -10
+#define ORA_LEMMA2 -11
+#define ORA_INV_PERM -12
+#define ORA_INV_PORDER -13
+#define ORA_INV_LASTPARTIAL -14
+#define ORA_INV_COUNT -15
+#define ORA_FIN_COUNT -16
+#define ORA_FIN_COPIES -17
+
+typedef struct {
+    uint64_t key;
+    uint32_t val;
+} elem_t;
+
+typedef struct {
+    uint64_t n_pi;          /* block count floor(n/b) + 2H */
+    uint64_t head;          /* H = sigma * p */
+    uint64_t t_blocks;      /* scratch blocks 2H */
+    uint64_t lemma1_checks; /* newBucketBlock calls beyond the initial sigma */
+    uint64_t min_unallocated; /* smallest unallocated count seen at fixup (Lemma 2) */
+    uint64_t fin_copies_main; /* block copies in Finalize's first loop */
+    uint64_t fin_copies_rest; /* block copies in Finalize's second loop */
+    uint64_t fin_pushes;
+    uint64_t extra_bytes;   /* T + bookkeeping, Sec. 3 "Space" / Sec. 4 */
+} ora_stats;
+
+/* ---- key positions (Sec. 1; reading G8) -------------------------------- */
+typedef struct {
+    int n_t;
+    uint32_t sigma;
+    int bits;        /* >0: d-bit digit fields; 0: key is a base-sigma numeral */
+} keyspec;
+
+static uint32_t key_at(const keyspec *ks, uint64_t k, int t)
+{
+#if ORACLE_MUTANT == 3
+    t = ks->n_t - 1 - t; /* planted mistake: digits numbered from the LSB */
+#endif
+    int pos = ks->n_t - 1 - t; /* number of digits below digit t */
+    if (ks->bits > 0) {
+        unsigned sh = (unsigned)(pos * ks->bits);
+        if (sh >= 64)
+            return 0;
+        return (uint32_t)((k >> sh) & (uint64_t)(ks->sigma - 1));
+    }
+    for (int i = 0; i < pos; i++)
+        k /= ks->sigma;
+    return (uint32_t)(k % ks->sigma);
+}
+
+static int check_spec(const keyspec *ks)
+{
+    if (ks->n_t < 1 || ks->n_t > 64 || ks->sigma < 1)
+        return ORA_EARG;
+    if (ks->bits > 0) {
+        if (ks->bits > 16 || ks->sigma != (1u << ks->bits))
+            return ORA_EARG;
+    } else if (ks->sigma < 2) {
+        return ORA_EARG;
+    }
+    return ORA_OK;
+}
+
+/* ======================================================================
+ * Alg. 1 -- out-of-place LSD radix sort round radixSortStep(A', A, t)
+ * ====================================================================== */
+static void radix_sort_step(elem_t *Ap, const elem_t *A, size_t n, const keyspec *ks, int t,
+                            size_t *H, size_t *S)
+{
+    for (uint32_t c = 0; c < ks->sigma; c++)
+        H[c] = 0;
+    for (size_t i = 0; i < n; i++) /* histogram of key(A[i], t) */
+        H[key_at(ks, A[i].key, t)]++;
+    S[0] = 0;
+    for (uint32_t c = 1; c < ks->sigma; c++) /* prefix sum over H */
+        S[c] = S[c - 1] + H[c - 1];
+#if ORACLE_MUTANT == 5
+    /* planted mistake: scatter walking the input backwards (unstable) */
+    for (size_t i = n; i-- > 0;) {
+        uint32_t c = key_at(ks, A[i].key, t);
+        Ap[S[c]++] = A[i];
+    }
+#else
+    for (size_t i = 0; i < n; i++) {
+        uint32_t c = key_at(ks, A[i].key, t); /* determine bucket */
+        Ap[S[c]] = A[i];                      /* sort A[i] into A' */
+        S[c]++;                               /* advance bucket c */
+    }
+#endif
+}
+
+/* keys/vals in place; `rounds` rounds for t = n_t-1, n_t-2, ... */
+int ora_lsd_oop(uint64_t *keys, uint32_t *vals, size_t n, int n_t, uint32_t sigma, int bits,
+                int rounds)
+{
+    keyspec ks = {n_t, sigma, bits};
+    if (check_spec(&ks) != ORA_OK || rounds < 0 || rounds > n_t)
+        return ORA_EARG;
+    if (n == 0)
+        return ORA_OK;
+    elem_t *A = malloc(n * sizeof(elem_t));
+    elem_t *Ap = malloc(n * sizeof(elem_t));
+    size_t *H = malloc(sigma * sizeof(size_t));
+    size_t *S = malloc(sigma * sizeof(size_t));
+    if (!A || !Ap || !H || !S) {
+        free(A), free(Ap), free(H), free(S);
+        return ORA_ENOMEM;
+    }
+    for (size_t i = 0; i < n; i++) {
+        A[i].key = keys[i];
+        A[i].val = vals ? vals[i] : 0;
+    }
+    for (int r = 0; r < rounds; r++) {
+        int t = n_t - 1 - r;
+        radix_sort_step(Ap, A, n, &ks, t, H, S);
+        elem_t *tmp = A;
+        A = Ap;
+        Ap = tmp;
+    }
+    for (size_t i = 0; i < n; i++) {
+        keys[i] = A[i].key;
+        if (vals)
+            vals[i] = A[i].val;
+    }
+    free(A), free(Ap), free(H), free(S);
+    return ORA_OK;
+}
+
+/* ======================================================================
+ * Radsort state (Sec. 2.1)
+ * ====================================================================== */
+typedef struct {
+    uint64_t idx; /* logical index */
+    uint64_t len; /* used elements, 0 <= len < b */
+} partial_t;
+
+typedef struct {
+    elem_t *next; /* p_next */
+    elem_t *end;  /* p_end */
+} bucket_t;
+
+typedef struct {
+    keyspec ks;
+    size_t n, b;
+    uint64_t p;     /* chunks (Sec. 4.3); 1 = sequential algorithm */
+    uint64_t H;     /* head start = sigma * p */
+    uint64_t n_pi;  /* floor(n/b) + 2H */
+    elem_t *A;      /* input / output array */
+    elem_t *T;      /* 2H scratch blocks */
+    uint64_t *pi;   /* logical index -> physical block */
+    uint64_t *pi2;  /* pi' (also reused for pi^-1 by Finalize) */
+    partial_t *P;   /* partial blocks, ascending logical index */
+    uint64_t nP;
+    uint64_t f;     /* fill level */
+    /* per-round, per-chunk scratch */
+    uint64_t *lo;   /* chunk bounds in logical block indices, p+1 entries */
+    uint64_t *C;    /* block counts, C[c*p + q] */
+    uint64_t *S;    /* bucket starts, S[c*p + q] */
+    bucket_t *B;    /* bucket allocation, B[q*sigma + c] */
+    uint32_t *U;    /* usage per free-list entry, U[q*U_stride + k] */
+    uint64_t U_stride;
+    uint64_t *iout; /* i_out per chunk */
+    ora_stats *st;
+} rs_t;
+
+static elem_t *blockat(rs_t *s, uint64_t i)
+{
+    if (i < 2 * s->H)
+        return &s->T[i * s->b];
+    return &s->A[(i - 2 * s->H) * s->b];
+}
+
+/* Alg. 3 with reading G1 */
+static uint64_t size_of_next_block(rs_t *s, uint64_t i, uint64_t *iP)
+{
+    if (*iP < s->nP && s->P[*iP].idx == i) {
+        uint64_t l = s->P[*iP].len;
+#if ORACLE_MUTANT == 6
+        /* planted mistake: the literal listing, length of the entry after */
+        if (*iP + 1 < s->nP)
+            l = s->P[*iP + 1].len;
+#endif
+        (*iP)++;
+        return l;
+    }
+    return s->b;
+}
+
+/* data invariant of Sec. 2.2 (clauses 1-3 and the element count of 5) */
+static int check_invariant(rs_t *s)
+{
+    uint8_t *seen = calloc(s->n_pi, 1);
+    if (!seen)
+        return ORA_ENOMEM;
+    for (uint64_t i = 0; i < s->n_pi; i++) {
+        if (s->pi[i] >= s->n_pi || seen[s->pi[i]]) {
+            free(seen);
+            return ORA_INV_PERM;
+        }
+        seen[s->pi[i]] = 1;
+    }
+    free(seen);
+    for (uint64_t j = 0; j < s->nP; j++) {
+        if (s->P[j].idx < s->H || s->P[j].idx >= s->f || s->P[j].len >= s->b)
+            return ORA_INV_PORDER;
+        if (j > 0 && s->P[j].idx <= s->P[j - 1].idx)
+            return ORA_INV_PORDER;
+    }
+    if (s->nP == 0 || s->P[s->nP - 1].idx != s->f - 1)
+        return ORA_INV_LASTPARTIAL;
+    uint64_t iP = 0, total = 0;
+    for (uint64_t i = s->H; i < s->f; i++)
+        total += size_of_next_block(s, i, &iP);
+    if (total != s->n)
+        return ORA_INV_COUNT;
+    return ORA_OK;
+}
+
+/* Alg. 4 (setup), head start H = sigma*p */
+static int setup(rs_t *s)
+{
+    uint64_t H = s->H, nb = s->n / s->b;
+    s->f = H + nb + 1;
+    for (uint64_t i = 0; i < H; i++) /* head start */
+        s->pi[i] = i;
+    for (uint64_t i = H; i + 1 < s->f; i++) /* contents of A */
+        s->pi[i] = 2 * H + (i - H);
+    for (uint64_t i = s->f - 1; i < s->n_pi; i++) /* remaining T blocks */
+        s->pi[i] = H + (i - (s->f - 1));
+    memset(s->T, 0xA5, 2 * H * s->b * sizeof(elem_t)); /* reading G9 */
+    memcpy(blockat(s, H), &s->A[nb * s->b], (s->n % s->b) * sizeof(elem_t)); /* tail */
+    s->P[0].idx = s->f - 1;
+    s->P[0].len = s->n % s->b;
+    s->nP = 1;
+    return check_invariant(s);
+}
+
+/* chunk bounds (Sec. 4.3): chunk q starts at the first logical block whose
+ * first element has position >= floor(q*n/p) in the current sequence. */
+static void make_chunks(rs_t *s)
+{
+    uint64_t q = 1, iP = 0, pos = 0;
+    s->lo[0] = s->H;
+    for (uint64_t i = s->H; i < s->f && q < s->p; i++) {
+        while (q < s->p && pos >= (uint64_t)(((unsigned __int128)q * s->n) / s->p))
+            s->lo[q++] = i;
+        pos += size_of_next_block(s, i, &iP);
+    }
+    while (q < s->p)
+        s->lo[q++] = s->f;
+    s->lo[s->p] = s->f;
+}
+
+static uint64_t free_list_entry(rs_t *s, uint64_t q, uint64_t k)
+{
+    uint32_t sigma = s->ks.sigma;
+    if (k < sigma)
+        return s->pi[q * sigma + k];
+    return s->pi[s->lo[q] + (k - sigma)];
+}
+
+/* newBucketBlock of Alg. 5, for chunk q.  i_in_fl is the free-list index of
+ * the next input block not yet fully read (reading G7 of Lemma 1: i_in as
+ * "next input block", which is the current block's index plus one once its
+ * last element has been copied). */
+static int new_bucket_block(rs_t *s, uint64_t q, uint32_t c, uint64_t i_in_fl)
+{
+    uint32_t sigma = s->ks.sigma;
+    uint64_t i_out = s->iout[q];
+    if (i_out >= sigma) { /* Lemma 1: i_out < i_in (free-list indices) */
+        s->st->lemma1_checks++;
+        if (!(i_out < i_in_fl))
+            return ORA_LEMMA1;
+    }
+    elem_t *pn = blockat(s, free_list_entry(s, q, i_out));
+    s->B[q * sigma + c].next = pn;
+    s->B[q * sigma + c].end = pn + s->b;
+    s->C[(uint64_t)c * s->p + q]++;
+    s->U[q * s->U_stride + i_out] = c;
+    s->iout[q] = i_out + 1;
+    return ORA_OK;
+}
+
+/* Alg. 5 (sortPhase) on every chunk in turn */
+static int sort_phase(rs_t *s, int t)
+{
+    uint32_t sigma = s->ks.sigma;
+    make_chunks(s);
+    memset(s->C, 0, (uint64_t)sigma * s->p * sizeof(uint64_t));
+    uint64_t iP = 0;
+    for (uint64_t q = 0; q < s->p; q++) {
+        s->iout[q] = 0;
+        for (uint32_t c = 0; c < sigma; c++) { /* initial output blocks */
+            int e = new_bucket_block(s, q, c, 0);
+            if (e)
+                return e;
+        }
+        for (uint64_t i_in = s->lo[q]; i_in < s->lo[q + 1]; i_in++) {
+            uint64_t fl_in = sigma + (i_in - s->lo[q]); /* i_in as free-list index */
+            elem_t *p_in = blockat(s, s->pi[i_in]);
+            uint64_t l = size_of_next_block(s, i_in, &iP);
+#if ORACLE_MUTANT == 1
+            l = s->b; /* planted mistake: partial blocks read as full */
+#endif
+            for (uint64_t j = 0; j < l; j++) {
+                uint32_t c = key_at(&s->ks, p_in[j].key, t);
+                bucket_t *bk = &s->B[q * sigma + c];
+                *bk->next = p_in[j]; /* copy p_in[j] to memory at p_next */
+                if (bk->next + 1 == bk->end) {
+                    int e = new_bucket_block(s, q, c, fl_in + (j + 1 == l ? 1 : 0));
+                    if (e)
+                        return e;
+                } else {
+                    bk->next++;
+                }
+            }
+        }
+    }
+    return ORA_OK;
+}
+
+/* Alg. 6 (fixupPhase), generalised to p chunks */
+static int fixup_phase(rs_t *s)
+{
+    uint32_t sigma = s->ks.sigma;
+    uint64_t G = (uint64_t)sigma * s->p;
+    uint64_t allocated = 0;
+    for (uint64_t q = 0; q < s->p; q++)
+        allocated += s->iout[q];
+    /* Lemma 2: at least H unallocated blocks */
+    uint64_t unalloc = s->n_pi - allocated;
+    if (unalloc < s->st->min_unallocated)
+        s->st->min_unallocated = unalloc;
+    if (unalloc < s->H)
+        return ORA_LEMMA2;
+    /* S: prefix sum over C plus the head start, bucket-major, chunk-minor */
+#if ORACLE_MUTANT == 2
+    /* planted mistake: chunk-major order of the groups */
+    {
+        uint64_t acc = s->H;
+        for (uint64_t q = 0; q < s->p; q++)
+            for (uint32_t c = 0; c < sigma; c++) {
+                s->S[(uint64_t)c * s->p + q] = acc;
+                acc += s->C[(uint64_t)c * s->p + q];
+            }
+    }
+#else
+    s->S[0] = s->H;
+    for (uint64_t g = 1; g < G; g++)
+        s->S[g] = s->S[g - 1] + s->C[g - 1];
+#endif
+    /* unallocated blocks: each chunk's unused free-list tail, then pi[f..) */
+    uint64_t nfree = 0, f_new = s->H + allocated;
+    for (uint64_t q = 0; q < s->p; q++) {
+        uint64_t fl_len = sigma + (s->lo[q + 1] - s->lo[q]);
+        for (uint64_t k = s->iout[q]; k < fl_len; k++, nfree++) {
+            uint64_t dst = nfree < s->H ? nfree : f_new + (nfree - s->H);
+            s->pi2[dst] = free_list_entry(s, q, k);
+        }
+    }
+    for (uint64_t i = s->f; i < s->n_pi; i++, nfree++) {
+        uint64_t dst = nfree < s->H ? nfree : f_new + (nfree - s->H);
+        s->pi2[dst] = s->pi[i];
+    }
+    if (nfree != unalloc)
+        return ORA_INV_COUNT;
+    /* shuffle used blocks into order of buckets; find the partial blocks */
+    for (uint64_t q = 0; q < s->p; q++) {
+        for (uint64_t k = 0; k < s->iout[q]; k++) {
+            uint32_t c = s->U[q * s->U_stride + k];
+            uint64_t g = (uint64_t)c * s->p + q;
+            uint64_t phys = free_list_entry(s, q, k);
+            s->pi2[s->S[g]] = phys;
+            bucket_t *bk = &s->B[q * sigma + c];
+            if (bk->end == blockat(s, phys) + s->b) { /* the open block? */
+                s->P[g].idx = s->S[g];
+                s->P[g].len = (uint64_t)(bk->next - blockat(s, phys));
+            }
+            s->S[g]++;
+        }
+    }
+    s->nP = G;
+    s->f = f_new;
+    uint64_t *tmp = s->pi;
+    s->pi = s->pi2;
+    s->pi2 = tmp;
+    return check_invariant(s);
+}
+
+/* Alg. 7 (swap and finalize), readings G2, G3, G6 */
+static void swap_blocks(rs_t *s, uint64_t *pinv, uint64_t i1, uint64_t j1, uint64_t i2, uint64_t j2)
+{
+    s->pi[i1] = j2;
+    s->pi[i2] = j1;
+    pinv[j1] = i2;
+    pinv[j2] = i1;
+}
+
+static int finalize(rs_t *s)
+{
+    uint64_t H = s->H, nb = s->n / s->b, b = s->b;
+    uint64_t *pinv = s->pi2; /* pi' reused for pi^-1 (Sec. 4) */
+    uint64_t k = 0, iP = 0;
+    uint64_t i_free = 0, j_free = s->pi[0]; /* unallocated as per invariant */
+    for (uint64_t i = 0; i < s->n_pi; i++)
+        pinv[s->pi[i]] = i;
+    for (uint64_t i_in = H; i_in < H + nb; i_in++) {
+        uint64_t j_in = s->pi[i_in];
+        uint64_t j_out = i_in + H; /* A block i_in - H (reading G2) */
+        uint64_t i_out = pinv[j_out];
+        if (i_in < i_out && i_out < s->f) { /* occupied by a block still needed */
+#if ORACLE_MUTANT != 4
+            memcpy(blockat(s, j_free), blockat(s, j_out), b * sizeof(elem_t)); /* push */
+#endif
+            s->st->fin_copies_main++;
+            s->st->fin_pushes++;
+            swap_blocks(s, pinv, i_out, j_out, i_free, j_free);
+            i_out = i_free; /* logical index now mapped to j_out (reading G3) */
+        }
+        uint64_t l = size_of_next_block(s, i_in, &iP);
+        memmove(&s->A[k], blockat(s, j_in), l * sizeof(elem_t)); /* pull (G6) */
+        s->st->fin_copies_main++;
+        k += l;
+        swap_blocks(s, pinv, i_out, j_out, i_in, j_in);
+        if (i_in != i_out) { /* pulled from elsewhere: j_in is now free */
+            i_free = i_out;
+            j_free = j_in;
+        }
+    }
+    for (uint64_t i_in = H + nb; i_in < s->f; i_in++) { /* remaining blocks, all in T */
+        uint64_t j_in = s->pi[i_in];
+        uint64_t l = size_of_next_block(s, i_in, &iP);
+        memmove(&s->A[k], blockat(s, j_in), l * sizeof(elem_t));
+        s->st->fin_copies_rest++;
+        k += l;
+    }
+    if (k != s->n)
+        return ORA_FIN_COUNT;
+    /* Sec. 3: at most two copies per A block, one per remaining block */
+    if (s->st->fin_copies_main > 2 * nb || s->st->fin_copies_rest > s->f - H - nb)
+        return ORA_FIN_COPIES;
+    return ORA_OK;
+}
+
+/* the permuted representation read in logical order (Sec. 4.1 iterator) */
+static void gather_sequence(rs_t *s, uint64_t *seq_keys, uint32_t *seq_vals)
+{
+    uint64_t iP = 0, k = 0;
+    for (uint64_t i = s->H; i < s->f; i++) {
+        elem_t *blk = blockat(s, s->pi[i]);
+        uint64_t l = size_of_next_block(s, i, &iP);
+        for (uint64_t j = 0; j < l; j++, k++) {
+            if (seq_keys)
+                seq_keys[k] = blk[j].key;
+            if (seq_vals)
+                seq_vals[k] = blk[j].val;
+        }
+    }
+}
+
+/*
+ * Alg. 2 (radSort).  Runs setup and `rounds` rounds (t = n_t-1 downwards).
+ * finalize != 0: Finalize, result in keys/vals (needs rounds == n_t for a
+ * full sort, but any rounds value is accepted).
+ * finalize == 0: the logical sequence after `rounds` rounds is written to
+ * seq_keys/seq_vals (n entries each, nullable) and keys/vals are untouched.
+ * elem_bytes only scales stats->extra_bytes.
+ */
+int ora_radsort(uint64_t *keys, uint32_t *vals, size_t n, int n_t, uint32_t sigma, int bits,
+                size_t b, uint64_t p, int rounds, int do_finalize, uint64_t *seq_keys,
+                uint32_t *seq_vals, uint64_t elem_bytes, ora_stats *st)
+{
+    keyspec ks = {n_t, sigma, bits};
+    ora_stats dummy;
+    if (!st)
+        st = &dummy;
+    memset(st, 0, sizeof(*st));
+    if (check_spec(&ks) != ORA_OK || b < 1 || p < 1 || rounds < 0 || rounds > n_t)
+        return ORA_EARG;
+    rs_t s;
+    memset(&s, 0, sizeof(s));
+    s.ks = ks;
+    s.n = n;
+    s.b = b;
+    s.p = p;
+    s.H = (uint64_t)sigma * p;
+    s.n_pi = n / b + 2 * s.H;
+    s.st = st;
+    st->n_pi = s.n_pi;
+    st->head = s.H;
+    st->t_blocks = 2 * s.H;
+    st->min_unallocated = UINT64_MAX;
+    uint64_t G = (uint64_t)sigma * p;
+    s.U_stride = sigma + n / b + G + 2; /* >= sigma + longest chunk */
+    s.A = malloc((n ? n : 1) * sizeof(elem_t));
+    s.T = malloc(2 * s.H * b * sizeof(elem_t));
+    s.pi = malloc(s.n_pi * sizeof(uint64_t));
+    s.pi2 = malloc(s.n_pi * sizeof(uint64_t));
+    s.P = malloc(G * sizeof(partial_t));
+    s.lo = malloc((p + 1) * sizeof(uint64_t));
+    s.C = malloc(G * sizeof(uint64_t));
+    s.S = malloc(G * sizeof(uint64_t));
+    s.B = malloc(G * sizeof(bucket_t));
+    s.U = malloc(p * s.U_stride * sizeof(uint32_t));
+    s.iout = malloc(p * sizeof(uint64_t));
+    int err = ORA_OK;
+    if (!s.A || !s.T || !s.pi || !s.pi2 || !s.P || !s.lo || !s.C || !s.S || !s.B || !s.U || !s.iout) {
+        err = ORA_ENOMEM;
+        goto out;
+    }
+    /* Sec. 3/4 space: T, pi, pi' (reused as pi^-1), U, P, B, C, S */
+    st->extra_bytes = 2 * s.H * b * elem_bytes + s.n_pi * (4 + 4 + (sigma <= 256 ? 1 : 2)) +
+                      G * (8 /*P*/ + 16 /*B*/ + 4 /*C*/ + 4 /*S*/);
+    for (size_t i = 0; i < n; i++) {
+        s.A[i].key = keys[i];
+        s.A[i].val = vals ? vals[i] : 0;
+    }
+    err = setup(&s);
+    for (int r = 0; r < rounds && !err; r++) {
+        err = sort_phase(&s, n_t - 1 - r);
+        if (!err)
+            err = fixup_phase(&s);
+    }
+    if (err)
+        goto out;
+    if (do_finalize) {
+        err = finalize(&s);
+        if (err)
+            goto out;
+        for (size_t i = 0; i < n; i++) {
+            keys[i] = s.A[i].key;
+            if (vals)
+                vals[i] = s.A[i].val;
+        }
+    } else {
+        gather_sequence(&s, seq_keys, seq_vals);
+    }
+out:
+    free(s.A), free(s.T), free(s.pi), free(s.pi2), free(s.P), free(s.lo);
+    free(s.C), free(s.S), free(s.B), free(s.U), free(s.iout);
+    return err;
+}
+
+/* order-preserving bit transform of float32 keys (not in the paper): the
+ * sign bit is flipped for non-negative values and every bit for negative
+ * ones, so that unsigned order of the result is the IEEE total order. */
+void ora_f32_to_ordered(uint32_t *u, size_t n)
+{
+    for (size_t i = 0; i < n; i++)
+        u[i] ^= (u[i] & 0x80000000u) ? 0xFFFFFFFFu : 0x80000000u;
+}
+
+void ora_ordered_to_f32(uint32_t *u, size_t n)
+{
+    for (size_t i = 0; i < n; i++)
+        u[i] ^= (u[i] & 0x80000000u) ? 0x80000000u : 0xFFFFFFFFu;
+}
+
+int ora_mutant_id(void) { return ORACLE_MUTANT; }
