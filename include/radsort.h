@@ -1,0 +1,138 @@
+/*
+ * radsort.h -- C ABI of the GB300 (sm_103a) Radsort library.
+ *
+ * Radsort ("Parallel O(sqrt n) Overhead LSD Radix Sort", Clausecker and
+ * Schintke) is a stable LSD radix sort. Instead of an n-element output
+ * buffer it uses a constant number of scratch blocks plus O(n/b)
+ * bookkeeping.
+ *
+ * Problem statement (Sec. 1): sort n elements whose keys are n_t-tuples over
+ * an alphabet of sigma symbols into lexicographic order, stably.  Here a key is
+ * an unsigned integer of key_bytes (4 or 8) read as n_t = ceil(8*key_bytes /
+ * digit_bits) digits of digit_bits bits each (sigma = 2^digit_bits), digit 0
+ * the most significant; the result is ascending unsigned order, stable, with
+ * the optional 32-bit values moved together with their keys.
+ *
+ * Conventions for every call below:
+ *  - keys / values / workspace are DEVICE pointers owned by the caller unless
+ *    stated; they must be 16-byte aligned (cudaMalloc and torch allocations
+ *    are); values may be NULL (keys only).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it asynchronously; the calls never synchronise it.
+ *  - Argument errors are returned synchronously and nothing is enqueued.
+ *    Errors detected on the device (a bounded wait that ran out, a violated
+ *    invariant) are recorded in a sticky library status word that
+ *    radsort_device_status() reads; the device never traps.
+ *  - n = 0 and n = 1 are no-ops that return RADSORT_OK.
+ */
+#ifndef RADSORT_H
+#define RADSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RADSORT_OK = 0,
+    RADSORT_EINVAL = 1,    /* bad argument (size, width, alignment, plan) */
+    RADSORT_ENOMEM = 2,    /* device allocation failed / workspace too small */
+    RADSORT_ECUDA = 3,     /* a CUDA runtime call failed */
+    RADSORT_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    RADSORT_EINTERNAL = 5  /* a device-side invariant check failed */
+} radsort_status;
+
+/* flags for radsort_sort_ex */
+#define RADSORT_KEY_FLOAT32 0x1u /* 4-byte keys are IEEE float32; sorted by the
+                                    total order (-NaN < -inf < ... < -0 < +0 <
+                                    ... < +inf < +NaN) via an order-preserving
+                                    bit transform applied before and undone
+                                    after the sort. */
+
+/* Tuning plan.  Zero fields mean "choose automatically". */
+typedef struct {
+    uint32_t block_size; /* b: elements per block, power of two in [64, 4096] */
+    uint32_t num_chunks; /* p: chunks sorted in parallel, each with its own
+                            head start of sigma blocks (Sec. 4.3) */
+    uint32_t reserved[6];
+} radsort_plan;
+
+/* Human-readable name of a status code (static storage). */
+const char *radsort_status_str(radsort_status s);
+
+/* Fills *plan with the automatic choice for these sizes. */
+radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, int digit_bits,
+                                    radsort_plan *plan);
+
+/*
+ * Bytes of device workspace radsort_sort_ex needs: the scratch array T of
+ * 2*sigma*p blocks (Sec. 2.1, Sec. 4.3), the block permutation pi and its
+ * successor, the usage array U (Alg. 5-6), the partial-block list P and the
+ * per-chunk counters.  This is the sort's whole extra device memory beyond
+ * the caller's arrays.  value_bytes is 0 or 4.
+ */
+radsort_status radsort_workspace_size(size_t n, int key_bytes, int value_bytes, int digit_bits,
+                                      const radsort_plan *plan, size_t *bytes);
+
+/*
+ * Alg. 2 (radSort): setup (Alg. 4), n_t rounds of sortPhase (Alg. 5) and
+ * fixupPhase (Alg. 6), then Finalize (Alg. 7), in place on keys[0..n) and
+ * values[0..n).  key_bytes: 4 or 8.  digit_bits: 8 (sigma = 256) or 11
+ * (sigma = 2048).  Allocates its workspace with cudaMallocAsync on `stream`
+ * and frees it the same way.
+ */
+radsort_status radsort_sort(void *keys, uint32_t *values, size_t n, int key_bytes, int digit_bits,
+                            void *stream);
+
+/*
+ * As radsort_sort, with flags (RADSORT_KEY_FLOAT32), an explicit plan
+ * (NULL = automatic) and a caller-provided workspace of at least
+ * radsort_workspace_size() bytes (NULL = allocate as radsort_sort does).
+ * The workspace must stay untouched until the sort has completed on `stream`.
+ */
+radsort_status radsort_sort_ex(void *keys, uint32_t *values, size_t n, int key_bytes,
+                               int digit_bits, uint32_t flags, const radsort_plan *plan,
+                               void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * The permuted representation without Finalize (Sec. 4.1, "Avoiding
+ * Finalisation"): runs setup and the first `rounds` rounds (0 <= rounds <= n_t)
+ * on keys/values in place, then writes the logical sequence -- the used
+ * elements of logical blocks sigma*p .. f-1 in order, each block's length
+ * given by sizeOfNextBlock (Alg. 3) -- to out_keys/out_values (n entries;
+ * out_values may be NULL).  keys/values are left in the block layout (their
+ * contents are unspecified afterwards).  After `rounds` rounds the sequence is
+ * the stable sort by the `rounds` least significant digits.
+ */
+radsort_status radsort_sort_rounds(void *keys, uint32_t *values, size_t n, int key_bytes,
+                                   int digit_bits, int rounds, const radsort_plan *plan,
+                                   void *out_keys, uint32_t *out_values, void *stream);
+
+/*
+ * Comparison baseline: a conventional out-of-place LSD radix sort, Alg. 1
+ * applied for t = n_t-1 .. 0, with one upfront pass that histograms all
+ * digits and a decoupled look-back scan per round.  keys_alt / values_alt are
+ * caller-provided n-element scratch arrays (the n*(key+value) bytes of extra
+ * memory that Radsort avoids); the result ends in keys / values.
+ */
+radsort_status radsort_lsd_oop_sort(void *keys, uint32_t *values, void *keys_alt,
+                                    uint32_t *values_alt, size_t n, int key_bytes, int digit_bits,
+                                    void *stream);
+
+/* Order-preserving bit transform for float32 keys, in place on the device:
+ * inverse = 0 maps IEEE bits to unsigned-orderable bits, inverse = 1 back. */
+radsort_status radsort_float_keys(uint32_t *keys, size_t n, int inverse, void *stream);
+
+/*
+ * Synchronises `stream`, returns the sticky device status accumulated by all
+ * sorts since the last call (RADSORT_OK if none failed), and clears it.
+ */
+radsort_status radsort_device_status(void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADSORT_H */

@@ -1,0 +1,368 @@
+// C ABI of the Radsort library (include/radsort.h): argument checks, the
+// planner (block size b and chunk count p), the workspace layout, and the
+// stream-ordered sequence setup -> n_t x (sortPhase, fixupPhase) -> Finalize
+// (Alg. 2).  Nothing here touches element data; every step runs in the
+// kernels of rs_round.cu and rs_finalize.cu.
+#include <cstdlib>
+#include <cstring>
+
+#include "radsort.h"
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 152;
+    }
+    return sms;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+static uint32_t ilog2(uint32_t x)
+{
+    uint32_t r = 0;
+    while ((1u << r) < x)
+        ++r;
+    return r;
+}
+
+static long env_long(const char *name, long dflt)
+{
+    const char *s = std::getenv(name);
+    return s && *s ? std::strtol(s, nullptr, 10) : dflt;
+}
+
+static size_t bookkeeping_per_block() { return 3 * 4; } // pi, pi', U
+
+// Automatic plan.  The scratch array costs 2*sigma*p*b*E bytes, so the
+// plan trades chunk parallelism p against block size b.  It targets 2% of
+// the array's bytes when the array is large enough, and otherwise falls
+// back to small p.
+static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
+{
+    const uint32_t sigma = 1u << db;
+    const size_t E = kb + vb;
+    const double budget = 0.0195 * double(n) * double(E); // 2% with margin for alignment
+    const uint32_t pmax = static_cast<uint32_t>(num_sms());
+    // at least ~64K elements per chunk
+    uint32_t pcap = static_cast<uint32_t>(n / 65536);
+    if (pcap > pmax)
+        pcap = pmax;
+    if (pcap < 1)
+        pcap = 1;
+    uint32_t best_b = 512, best_p = 1;
+    const uint32_t cands[] = {256, 512, 1024, 2048};
+    for (uint32_t b : cands) {
+        if (db == 11 && n / b >= (1u << 20))
+            continue; // sequence numbers of a chunk's blocks need < 2^21
+        const double fixed = double(n / b) * bookkeeping_per_block();
+        const double per_p = 2.0 * sigma * b * double(E) + sigma * 24.0;
+        double pf = (budget - fixed) / per_p;
+        uint32_t p = pf < 1 ? 1 : (pf > pcap ? pcap : static_cast<uint32_t>(pf));
+        if (p > best_p || (p == best_p && b < best_b && best_p == 1)) {
+            best_p = p;
+            best_b = b;
+        }
+    }
+    if (best_p == 1 && n < (size_t(1) << 22))
+        best_b = 256;
+    pl->block_size = best_b;
+    pl->num_chunks = best_p;
+    long eb = env_long("RADSORT_B", 0), ep = env_long("RADSORT_P", 0);
+    if (eb > 0)
+        pl->block_size = static_cast<uint32_t>(eb);
+    if (ep > 0)
+        pl->num_chunks = static_cast<uint32_t>(ep);
+}
+
+static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radsort_plan *plan,
+                                Geom *g)
+{
+    if ((kb != 4 && kb != 8) || (db != 8 && db != 11))
+        return RADSORT_EINVAL;
+    radsort_plan pl{};
+    auto_plan(n, kb, hasv ? 4 : 0, db, &pl);
+    if (plan && plan->block_size)
+        pl.block_size = plan->block_size;
+    if (plan && plan->num_chunks)
+        pl.num_chunks = plan->num_chunks;
+    const uint32_t b = pl.block_size, p = pl.num_chunks;
+    if (!pow2(b) || b < 64 || b > 4096 || p < 1 || p > 65536)
+        return RADSORT_EINVAL;
+    g->n = n;
+    g->kb = kb;
+    g->hasv = hasv;
+    g->db = db;
+    g->sigma = 1u << db;
+    g->nt = (8 * kb + db - 1) / db;
+    g->b = b;
+    g->lb = ilog2(b);
+    g->p = p;
+    const unsigned long long nA = n / b;
+    const unsigned long long H = (unsigned long long)g->sigma * p;
+    const unsigned long long npi = nA + 2 * H;
+    if (npi >= (1ull << 30))
+        return RADSORT_EINVAL; // 32-bit block indices with flag bits to spare
+    // sequence number of a block in its chunk's bucket chain: < 2^(32-db)
+    if ((unsigned long long)g->sigma + npi >= (1ull << (32 - db)))
+        return RADSORT_EINVAL;
+    g->nA = static_cast<uint32_t>(nA);
+    g->H = static_cast<uint32_t>(H);
+    g->nT = static_cast<uint32_t>(2 * H);
+    g->npi = static_cast<uint32_t>(npi);
+    g->G = static_cast<uint32_t>(H);
+    return RADSORT_OK;
+}
+
+// Carves the workspace; with base == nullptr only computes the size.
+static size_t layout(const Geom &g, void *base, Bufs *w)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        off = align_up(off, 256);
+        void *p = base ? static_cast<char *>(base) + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t tel = size_t(g.nT) * g.b;
+    const size_t npi2 = g.npi + (g.npi & 1);
+    Bufs b{};
+    b.Tk = take(tel * g.kb);
+    b.Tv = static_cast<uint32_t *>(g.hasv ? take(tel * 4) : nullptr);
+    b.aux = static_cast<uint32_t *>(take(3 * npi2 * 4));
+    b.C = static_cast<uint32_t *>(take(size_t(g.G) * 4));
+    b.FILL = static_cast<uint32_t *>(take(size_t(g.G) * 4));
+    b.S = static_cast<uint32_t *>(take(size_t(g.G) * 4));
+    b.P = static_cast<uint2 *>(take(size_t(g.G) * 8));
+    b.E = static_cast<unsigned long long *>(take(size_t(g.G + 1) * 8));
+    b.lo0 = static_cast<uint32_t *>(take(size_t(g.p + 1) * 4));
+    b.lo1 = static_cast<uint32_t *>(take(size_t(g.p + 1) * 4));
+    b.Aal = static_cast<uint32_t *>(take(size_t(g.p) * 4));
+    b.LOff = static_cast<uint32_t *>(take(size_t(g.p + 1) * 4));
+    b.state = static_cast<uint32_t *>(take(ST_WORDS * 4));
+    void *fin = take(finalize_extra_bytes(g));
+    (void)fin;
+    off = align_up(off, 256);
+    if (w)
+        *w = b;
+    return off;
+}
+
+static cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+static radsort_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return RADSORT_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return RADSORT_ENOMEM;
+    return RADSORT_ECUDA;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Runs setup and `rounds` rounds; returns the current pi buffer through *pi_cur.
+static cudaError_t run_rounds(const Geom &g, Bufs &w, int rounds, cudaStream_t st,
+                              uint32_t **pi_cur, uint32_t **pi_oth)
+{
+    const size_t npi2 = g.npi + (g.npi & 1);
+    uint32_t *piX = w.aux, *UC = w.aux + npi2, *piY = w.aux + 2 * npi2;
+    uint32_t *pc = piX, *pn = piY, *lc = w.lo0, *ln = w.lo1;
+    cudaError_t e = launch_setup(g, w, pc, st);
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+        e = launch_round(g, w, pc, lc, UC, r, st);
+        if (e == cudaSuccess)
+            e = launch_fixup(g, w, pc, pn, UC, lc, ln, st);
+        uint32_t *t = pc;
+        pc = pn;
+        pn = t;
+        t = lc;
+        lc = ln;
+        ln = t;
+    }
+    *pi_cur = pc;
+    *pi_oth = pn;
+    return e;
+}
+
+} // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+const char *radsort_status_str(radsort_status s)
+{
+    switch (s) {
+    case RADSORT_OK: return "ok";
+    case RADSORT_EINVAL: return "invalid argument";
+    case RADSORT_ENOMEM: return "out of device memory / workspace too small";
+    case RADSORT_ECUDA: return "CUDA runtime error";
+    case RADSORT_ETIMEOUT: return "bounded device wait ran out";
+    case RADSORT_EINTERNAL: return "device invariant check failed";
+    }
+    return "unknown status";
+}
+
+radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, int digit_bits,
+                                    radsort_plan *plan)
+{
+    if (!plan || (key_bytes != 4 && key_bytes != 8) || (value_bytes != 0 && value_bytes != 4) ||
+        (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    std::memset(plan, 0, sizeof(*plan));
+    auto_plan(n, key_bytes, value_bytes, digit_bits, plan);
+    return RADSORT_OK;
+}
+
+radsort_status radsort_workspace_size(size_t n, int key_bytes, int value_bytes, int digit_bits,
+                                      const radsort_plan *plan, size_t *bytes)
+{
+    if (!bytes || (value_bytes != 0 && value_bytes != 4))
+        return RADSORT_EINVAL;
+    *bytes = 0;
+    if (n <= 1)
+        return RADSORT_OK;
+    Geom g;
+    radsort_status s = make_geom(n, key_bytes, value_bytes == 4, digit_bits, plan, &g);
+    if (s != RADSORT_OK)
+        return s;
+    *bytes = layout(g, nullptr, nullptr);
+    return RADSORT_OK;
+}
+
+static radsort_status sort_common(void *keys, uint32_t *values, size_t n, int key_bytes,
+                                  int digit_bits, uint32_t flags, const radsort_plan *plan,
+                                  void *workspace, size_t workspace_bytes, void *stream,
+                                  int rounds, void *out_keys, uint32_t *out_values)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if ((flags & RADSORT_KEY_FLOAT32) && key_bytes != 4)
+        return RADSORT_EINVAL;
+    if (flags & ~RADSORT_KEY_FLOAT32)
+        return RADSORT_EINVAL;
+    if (n <= 1 && rounds < 0)
+        return RADSORT_OK;
+    if (!keys || !aligned16(keys) || (values && !aligned16(values)))
+        return RADSORT_EINVAL;
+    Geom g;
+    radsort_status s = make_geom(n < 2 ? 2 : n, key_bytes, values != nullptr, digit_bits, plan, &g);
+    if (s != RADSORT_OK)
+        return s;
+    g.n = n;
+    g.nA = static_cast<uint32_t>(n / g.b);
+    g.npi = g.nA + g.nT;
+    if (rounds > g.nt)
+        return RADSORT_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const size_t need = layout(g, nullptr, nullptr);
+    void *ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (workspace_bytes < need || !aligned16(ws))
+            return workspace_bytes < need ? RADSORT_ENOMEM : RADSORT_EINVAL;
+    } else {
+        cudaError_t e = cudaMallocAsync(&ws, need, st);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        own = true;
+    }
+    Bufs w;
+    layout(g, ws, &w);
+    w.Ak = keys;
+    w.Av = values;
+    cudaError_t e = cudaSuccess;
+    if (flags & RADSORT_KEY_FLOAT32)
+        e = launch_float_keys(static_cast<uint32_t *>(keys), n, 0, st);
+    uint32_t *pc = nullptr, *po = nullptr;
+    if (e == cudaSuccess)
+        e = run_rounds(g, w, rounds < 0 ? g.nt : rounds, st, &pc, &po);
+    if (e == cudaSuccess) {
+        if (rounds < 0)
+            e = launch_finalize(g, w, pc, po, st);
+        else
+            e = launch_gather(g, w, pc, out_keys, out_values, st);
+    }
+    if (e == cudaSuccess && (flags & RADSORT_KEY_FLOAT32) && rounds < 0)
+        e = launch_float_keys(static_cast<uint32_t *>(keys), n, 1, st);
+    if (own) {
+        cudaError_t e2 = cudaFreeAsync(ws, st);
+        if (e == cudaSuccess)
+            e = e2;
+    }
+    return cuda_status(e);
+}
+
+radsort_status radsort_sort_ex(void *keys, uint32_t *values, size_t n, int key_bytes,
+                               int digit_bits, uint32_t flags, const radsort_plan *plan,
+                               void *workspace, size_t workspace_bytes, void *stream)
+{
+    return sort_common(keys, values, n, key_bytes, digit_bits, flags, plan, workspace,
+                       workspace_bytes, stream, -1, nullptr, nullptr);
+}
+
+radsort_status radsort_sort(void *keys, uint32_t *values, size_t n, int key_bytes, int digit_bits,
+                            void *stream)
+{
+    return sort_common(keys, values, n, key_bytes, digit_bits, 0, nullptr, nullptr, 0, stream, -1,
+                       nullptr, nullptr);
+}
+
+radsort_status radsort_sort_rounds(void *keys, uint32_t *values, size_t n, int key_bytes,
+                                   int digit_bits, int rounds, const radsort_plan *plan,
+                                   void *out_keys, uint32_t *out_values, void *stream)
+{
+    if (rounds < 0 || !out_keys || !aligned16(out_keys) || (out_values && !values))
+        return RADSORT_EINVAL;
+    if (n == 0)
+        return RADSORT_OK;
+    return sort_common(keys, values, n, key_bytes, digit_bits, 0, plan, nullptr, 0, stream, rounds,
+                       out_keys, out_values);
+}
+
+radsort_status radsort_float_keys(uint32_t *keys, size_t n, int inverse, void *stream)
+{
+    if (n && !keys)
+        return RADSORT_EINVAL;
+    return cuda_status(launch_float_keys(keys, n, inverse, as_stream(stream)));
+}
+
+radsort_status radsort_lsd_oop_sort(void *keys, uint32_t *values, void *keys_alt,
+                                    uint32_t *values_alt, size_t n, int key_bytes, int digit_bits,
+                                    void *stream)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (n <= 1)
+        return RADSORT_OK;
+    if (!keys || !keys_alt || (values && !values_alt))
+        return RADSORT_EINVAL;
+    return cuda_status(
+        launch_lsd_oop(keys, values, keys_alt, values_alt, n, key_bytes, digit_bits, as_stream(stream)));
+}
+
+radsort_status radsort_device_status(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    const unsigned v = take_status_round() | take_status_finalize() | take_status_oop();
+    if (v & ST_TIMEOUT)
+        return RADSORT_ETIMEOUT;
+    if (v & ST_INTERNAL)
+        return RADSORT_EINTERNAL;
+    return RADSORT_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,88 @@
+// Kernel launchers of the Radsort library (host side declarations).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rs {
+
+// bits of the device status words
+enum : unsigned { ST_TIMEOUT = 1u, ST_INTERNAL = 2u };
+
+// Sizes of one sort (host view).  Block indices are 32-bit.
+struct Geom {
+    size_t n;          // elements
+    int kb;            // key bytes 4 | 8
+    bool hasv;         // 32-bit values present
+    int db;            // digit bits 8 | 11
+    uint32_t sigma;    // 2^db
+    int nt;            // digits per key
+    uint32_t b, lb;    // block size and log2
+    uint32_t p;        // chunks
+    uint32_t nA;       // floor(n/b): blocks overlaying A
+    uint32_t H;        // head start sigma*p
+    uint32_t nT;       // scratch blocks 2H
+    uint32_t npi;      // nA + 2H
+    uint32_t G;        // groups (bucket, chunk) = sigma*p
+};
+
+// Device buffers of one sort, carved from one workspace allocation.
+struct Bufs {
+    void *Ak;          // caller's keys
+    uint32_t *Av;      // caller's values (nullable)
+    void *Tk;          // scratch keys, nT*b
+    uint32_t *Tv;      // scratch values, nT*b (nullable)
+    uint32_t *aux;     // [piX | UC | piY]: 3*npi words (pi ping-pong around UC)
+    uint32_t *C;       // G  block counts, bucket-major (c*p + q)
+    uint32_t *FILL;    // G  open-block fill
+    uint32_t *S;       // G  group start (logical index)
+    uint2 *P;          // G  partial blocks (logical index, length)
+    unsigned long long *E; // G group first element position
+    uint32_t *lo0, *lo1;   // p+1 chunk bounds (ping-pong)
+    uint32_t *Aal;     // p   allocations per chunk
+    uint32_t *LOff;    // p+1 leftover offsets
+    uint32_t *state;   // scalars, see ST_*
+    // Finalize
+    unsigned long long *jump; // npi (aliases aux, see finalize)
+    uint32_t *fin_ctr;        // counters and flags used by Finalize
+    size_t fin_ctr_words;
+    void *slot_k;             // long-cycle save slots
+    uint32_t *slot_v;
+    uint32_t nslots;
+    uint32_t *cycles;         // long-cycle table (g0, len) pairs
+    uint32_t *flags;          // per-stride / per-window progress flags
+    size_t nflags;
+};
+
+// indices into Bufs::state
+enum { ST_F = 0, ST_NP = 1, ST_FPREV = 2, ST_LOFFTOT = 3, ST_WORDS = 8 };
+
+// setup (Alg. 4) + chunk bounds of round 0
+cudaError_t launch_setup(const Geom &g, const Bufs &w, uint32_t *pi, cudaStream_t st);
+// one sortPhase (Alg. 5) over p chunks
+cudaError_t launch_round(const Geom &g, const Bufs &w, const uint32_t *pi, const uint32_t *lo,
+                         uint32_t *UC, int round, cudaStream_t st);
+// fixupPhase (Alg. 6): scan + placement into pi_new
+cudaError_t launch_fixup(const Geom &g, const Bufs &w, const uint32_t *pi_old, uint32_t *pi_new,
+                         const uint32_t *UC, const uint32_t *lo_old, uint32_t *lo_new,
+                         cudaStream_t st);
+// gather of the logical sequence (Sec. 4.1 iterator)
+cudaError_t launch_gather(const Geom &g, const Bufs &w, const uint32_t *pi, void *out_k,
+                          uint32_t *out_v, cudaStream_t st);
+// Finalize (Alg. 7 semantics): pi applied to the data in place
+cudaError_t launch_finalize(const Geom &g, const Bufs &w, uint32_t *pi, uint32_t *pi_other,
+                            cudaStream_t st);
+size_t finalize_extra_bytes(const Geom &g);
+// float32 key transform
+cudaError_t launch_float_keys(uint32_t *keys, size_t n, int inverse, cudaStream_t st);
+// out-of-place LSD comparator
+cudaError_t launch_lsd_oop(void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
+                           size_t n, int kb, int db, cudaStream_t st);
+
+int num_sms();
+// read and clear the device status words of each translation unit
+unsigned take_status_round();
+unsigned take_status_finalize();
+unsigned take_status_oop();
+
+} // namespace rs

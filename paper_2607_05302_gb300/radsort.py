@@ -1,0 +1,186 @@
+"""Python binding of the C ABI in include/radsort.h (ctypes).
+
+Argument marshalling only: every step of the sort runs in the CUDA library
+libradsort_gb300.so built in-tree by paper_2607_05302_gb300/build.py.  If the
+library is missing this module raises.  There is no CPU fallback.
+
+The entry points keep the C names and take raw device pointers (ints).  The
+`*_tensors` helpers pass torch tensors' data pointers and the current CUDA
+stream.  torch supplies memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libradsort_gb300.so")
+
+RADSORT_OK, RADSORT_EINVAL, RADSORT_ENOMEM, RADSORT_ECUDA, RADSORT_ETIMEOUT, RADSORT_EINTERNAL = range(6)
+RADSORT_KEY_FLOAT32 = 0x1
+
+
+class RadsortError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class Plan(ctypes.Structure):
+    _fields_ = [("block_size", ctypes.c_uint32), ("num_chunks", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library {LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; "
+                f"g.build()'` first (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, sz, i, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32
+        pplan = ctypes.POINTER(Plan)
+        sig = {
+            "radsort_status_str": ([i], ctypes.c_char_p),
+            "radsort_plan_default": ([sz, i, i, i, pplan], i),
+            "radsort_workspace_size": ([sz, i, i, i, pplan, ctypes.POINTER(sz)], i),
+            "radsort_sort": ([vp, vp, sz, i, i, vp], i),
+            "radsort_sort_ex": ([vp, vp, sz, i, i, u32, pplan, vp, sz, vp], i),
+            "radsort_sort_rounds": ([vp, vp, sz, i, i, i, pplan, vp, vp, vp], i),
+            "radsort_lsd_oop_sort": ([vp, vp, vp, vp, sz, i, i, vp], i),
+            "radsort_float_keys": ([vp, sz, i, vp], i),
+            "radsort_device_status": ([vp], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+# exported names declared in include/radsort.h
+EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_workspace_size", "radsort_sort",
+           "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort", "radsort_float_keys",
+           "radsort_device_status")
+
+
+def status_str(s: int) -> str:
+    return lib().radsort_status_str(s).decode()
+
+
+def _ok(s: int, what: str):
+    if s != RADSORT_OK:
+        raise RadsortError(s, what)
+
+
+def _plan(block_size=0, num_chunks=0):
+    if not block_size and not num_chunks:
+        return None
+    p = Plan()
+    p.block_size = block_size
+    p.num_chunks = num_chunks
+    return ctypes.byref(p)
+
+
+# ---------------------------------------------------------------- raw C names
+def radsort_plan_default(n, key_bytes, value_bytes, digit_bits):
+    p = Plan()
+    _ok(lib().radsort_plan_default(n, key_bytes, value_bytes, digit_bits, ctypes.byref(p)),
+        "radsort_plan_default")
+    return int(p.block_size), int(p.num_chunks)
+
+
+def radsort_workspace_size(n, key_bytes, value_bytes, digit_bits, block_size=0, num_chunks=0):
+    out = ctypes.c_size_t(0)
+    _ok(lib().radsort_workspace_size(n, key_bytes, value_bytes, digit_bits,
+                                     _plan(block_size, num_chunks), ctypes.byref(out)),
+        "radsort_workspace_size")
+    return int(out.value)
+
+
+def radsort_sort(keys, values, n, key_bytes, digit_bits, stream):
+    _ok(lib().radsort_sort(keys, values, n, key_bytes, digit_bits, stream), "radsort_sort")
+
+
+def radsort_sort_ex(keys, values, n, key_bytes, digit_bits, flags=0, block_size=0, num_chunks=0,
+                    workspace=None, workspace_bytes=0, stream=None):
+    _ok(lib().radsort_sort_ex(keys, values, n, key_bytes, digit_bits, flags,
+                              _plan(block_size, num_chunks), workspace, workspace_bytes, stream),
+        "radsort_sort_ex")
+
+
+def radsort_sort_rounds(keys, values, n, key_bytes, digit_bits, rounds, out_keys, out_values,
+                        block_size=0, num_chunks=0, stream=None):
+    _ok(lib().radsort_sort_rounds(keys, values, n, key_bytes, digit_bits, rounds,
+                                  _plan(block_size, num_chunks), out_keys, out_values, stream),
+        "radsort_sort_rounds")
+
+
+def radsort_lsd_oop_sort(keys, values, keys_alt, values_alt, n, key_bytes, digit_bits, stream):
+    _ok(lib().radsort_lsd_oop_sort(keys, values, keys_alt, values_alt, n, key_bytes, digit_bits,
+                                   stream), "radsort_lsd_oop_sort")
+
+
+def radsort_float_keys(keys, n, inverse, stream):
+    _ok(lib().radsort_float_keys(keys, n, inverse, stream), "radsort_float_keys")
+
+
+def radsort_device_status(stream=None):
+    _ok(lib().radsort_device_status(stream), "device status")
+
+
+# ---------------------------------------------------------------- torch helpers
+def _torch_stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _key_bytes(t):
+    import torch
+    kb = {torch.int32: 4, torch.uint32: 4, torch.float32: 4, torch.int64: 8, torch.uint64: 8}.get(t.dtype)
+    if kb is None:
+        raise TypeError(f"unsupported key dtype {t.dtype}")
+    return kb
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def sort_tensors(keys, values=None, *, digit_bits=8, float_keys=False, block_size=0, num_chunks=0,
+                 workspace=None, stream=None):
+    """In-place stable Radsort of CUDA tensors (keys: 32/64-bit, read as
+    unsigned; values: optional 32-bit)."""
+    assert keys.is_cuda and keys.is_contiguous()
+    n = keys.numel()
+    if values is not None:
+        assert values.is_cuda and values.is_contiguous() and values.numel() == n
+        assert values.element_size() == 4
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    radsort_sort_ex(_ptr(keys), _ptr(values), n, _key_bytes(keys), digit_bits,
+                    RADSORT_KEY_FLOAT32 if float_keys else 0, block_size, num_chunks, ws, wsb,
+                    _torch_stream(stream))
+
+
+def sort_rounds_tensors(keys, values, rounds, out_keys, out_values=None, *, digit_bits=8,
+                        block_size=0, num_chunks=0, stream=None):
+    radsort_sort_rounds(_ptr(keys), _ptr(values), keys.numel(), _key_bytes(keys), digit_bits, rounds,
+                        _ptr(out_keys), _ptr(out_values), block_size, num_chunks,
+                        _torch_stream(stream))
+
+
+def lsd_oop_tensors(keys, values, keys_alt, values_alt, *, digit_bits=8, stream=None):
+    radsort_lsd_oop_sort(_ptr(keys), _ptr(values), _ptr(keys_alt), _ptr(values_alt), keys.numel(),
+                         _key_bytes(keys), digit_bits, _torch_stream(stream))
+
+
+def float_keys_tensors(keys, inverse=False, stream=None):
+    radsort_float_keys(_ptr(keys), keys.numel(), 1 if inverse else 0, _torch_stream(stream))

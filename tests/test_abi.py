@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function include/radsort.h declares; argument errors come back synchronously
+(no GPU needed for those)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_05302_gb300 import build as B
+    from paper_2607_05302_gb300 import radsort as R
+
+    B.build()
+    return R.lib()
+
+
+def header_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(radsort_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_expected_calls():
+    names = header_functions()
+    for must in ("radsort_sort", "radsort_sort_ex", "radsort_workspace_size",
+                 "radsort_lsd_oop_sort", "radsort_sort_rounds", "radsort_device_status"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+    from paper_2607_05302_gb300 import radsort as R
+    assert set(R.EXPORTS) <= set(header_functions())
+
+
+def test_synchronous_argument_errors(lib):
+    from paper_2607_05302_gb300 import radsort as R
+
+    bad = ctypes.c_void_p(16)
+    assert lib.radsort_sort(bad, None, 100, 3, 8, None) == R.RADSORT_EINVAL   # key width
+    assert lib.radsort_sort(bad, None, 100, 4, 9, None) == R.RADSORT_EINVAL   # digit width
+    assert lib.radsort_sort(ctypes.c_void_p(18), None, 100, 4, 8, None) == R.RADSORT_EINVAL  # alignment
+    assert lib.radsort_sort(None, None, 0, 4, 8, None) == R.RADSORT_OK        # n = 0
+    assert lib.radsort_sort(None, None, 1, 4, 8, None) == R.RADSORT_OK        # n = 1
+    assert lib.radsort_sort_ex(bad, None, 100, 8, 8, R.RADSORT_KEY_FLOAT32, None, None, 0,
+                               None) == R.RADSORT_EINVAL  # float flag needs 4-byte keys
+    p = R.Plan()
+    p.block_size = 100  # not a power of two
+    assert lib.radsort_sort_ex(bad, None, 1000, 4, 8, 0, ctypes.byref(p), None, 0,
+                               None) == R.RADSORT_EINVAL
+    assert R.status_str(R.RADSORT_ETIMEOUT) == "bounded device wait ran out"
+
+
+def test_workspace_size_matches_space_analysis(lib):
+    """Sec. 3: the workspace is T (2*sigma*p blocks of b elements) plus O(n/b)
+    bookkeeping; at 2^30 8-byte elements the automatic plan stays within 2%."""
+    from paper_2607_05302_gb300 import radsort as R
+
+    n = 1 << 30
+    b, p = R.radsort_plan_default(n, 4, 4, 8)
+    ws = R.radsort_workspace_size(n, 4, 4, 8)
+    T = 2 * 256 * p * b * 8
+    assert T <= ws <= T + (n // b) * 64 + 256 * p * 64 + (1 << 20)
+    assert ws <= 0.02 * n * 8
+    ws2 = R.radsort_workspace_size(1 << 20, 4, 4, 8, block_size=1024, num_chunks=2)
+    assert ws2 >= 2 * 256 * 2 * 1024 * 8

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA Radsort (through the C ABI) against the oracle, element
+by element, bit-exact (the result of a stable sort is unique, so there is no
+tolerance).  Sizes span several tiles and chunks with ragged tails; the
+launch configurations include the automatic plan that bench.py uses."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_05302_gb300 import radsort as R
+from paper_2607_05302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def to_dev(a):
+    return torch.from_numpy(a.view(np.int32 if a.dtype == np.uint32 else np.int64)).to(DEV)
+
+
+def from_dev(t, dtype):
+    return t.cpu().numpy().view(dtype)
+
+
+def gpu_sort(keys, vals, digit_bits=8, float_keys=False, block_size=0, num_chunks=0):
+    kt = to_dev(keys)
+    vt = None if vals is None else to_dev(vals)
+    R.sort_tensors(kt, vt, digit_bits=digit_bits, float_keys=float_keys, block_size=block_size,
+                   num_chunks=num_chunks)
+    R.radsort_device_status()
+    return from_dev(kt, keys.dtype), (None if vt is None else from_dev(vt, np.uint32))
+
+
+def oracle_sort(keys, vals, key_bits, digit_bits):
+    n_t = oracle.digits_for(key_bits, digit_bits)
+    k, v = oracle.radsort(keys, vals, n_t=n_t, sigma=1 << digit_bits, bits=digit_bits, b=256, p=1,
+                          elem_bytes=key_bits // 8 + 4)
+    return k.astype(keys.dtype), v
+
+
+SIZES = [2, 3, 63, 64, 65, 255, 256, 257, 4095, 4096, 4097, 10000, 65543, 300001]
+PLANS = [(64, 1), (64, 3), (256, 2), (1024, 4), (4096, 1), (0, 0)]
+
+
+@pytest.mark.parametrize("plan", PLANS)
+@pytest.mark.parametrize("n", SIZES)
+def test_u32_d8_ragged(n, plan):
+    rng = np.random.default_rng(n)
+    for keys in (rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32),
+                 rng.integers(0, 700, n, dtype=np.uint64).astype(np.uint32)):
+        vals = W.index_payload(n)
+        gk, gv = gpu_sort(keys, vals, block_size=plan[0], num_chunks=plan[1])
+        ek, ev = oracle_sort(keys, vals, 32, 8)
+        assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("plan", [(64, 3), (256, 5), (1024, 2)])
+def test_logical_sequence_each_round(plan):
+    """After r rounds the permuted representation (Sec. 4.1) read in logical
+    order equals r rounds of Alg. 1 in the oracle."""
+    n = 50001
+    keys = W.make_keys("uniform", n)
+    keys[::3] = keys[1]  # ties
+    vals = W.index_payload(n)
+    for r in range(5):
+        kt, vt = to_dev(keys), to_dev(vals)
+        ok = torch.empty_like(kt)
+        ov = torch.empty_like(vt)
+        R.sort_rounds_tensors(kt, vt, r, ok, ov, digit_bits=8, block_size=plan[0], num_chunks=plan[1])
+        R.radsort_device_status()
+        lk, lv = oracle.lsd_oop(keys, vals, n_t=4, sigma=256, bits=8, rounds=r)
+        assert np.array_equal(from_dev(ok, np.uint32), lk.astype(np.uint32))
+        assert np.array_equal(from_dev(ov, np.uint32), lv)
+
+
+@pytest.mark.parametrize("dist", W.DISTRIBUTIONS)
+def test_config1_distributions(dist):
+    """n = 2^20 uint32 keys + index payload, sigma = 256, b = 1024."""
+    n = 1 << 20
+    keys = W.make_keys(dist, n)
+    vals = W.index_payload(n)
+    fl = dist == "float"
+    gk, gv = gpu_sort(keys, vals, float_keys=fl, block_size=1024, num_chunks=8)
+    ok_keys = oracle.f32_to_ordered(keys) if fl else keys
+    ek, ev = oracle_sort(ok_keys, vals, 32, 8)
+    if fl:
+        ek = oracle.ordered_to_f32(ek)
+    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("digit_bits", [8, 11])
+@pytest.mark.parametrize("with_vals", [True, False])
+@pytest.mark.parametrize("plan", [(256, 3), (2048, 2), (0, 0)])
+def test_u64(digit_bits, with_vals, plan):
+    n = 200003
+    keys = W.make_keys("uniform", n, 64)
+    keys[::11] = keys[5]
+    vals = W.index_payload(n) if with_vals else None
+    gk, gv = gpu_sort(keys, vals, digit_bits=digit_bits, block_size=plan[0], num_chunks=plan[1])
+    ek, ev = oracle_sort(keys, vals, 64, digit_bits)
+    assert np.array_equal(gk, ek)
+    if with_vals:
+        assert np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("plan", [(256, 4), (512, 1)])
+def test_u32_d11_and_keys_only(plan):
+    n = 123457
+    keys = W.make_keys("zipf", n)
+    gk, _ = gpu_sort(keys, None, digit_bits=11, block_size=plan[0], num_chunks=plan[1])
+    assert np.array_equal(gk, np.sort(keys))
+    vals = W.index_payload(n)
+    gk, gv = gpu_sort(keys, vals, digit_bits=11, block_size=plan[0], num_chunks=plan[1])
+    ek, ev = oracle_sort(keys, vals, 32, 11)
+    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
+def test_caller_workspace_and_small_n():
+    n = 77777
+    keys = W.make_keys("reverse", n)
+    vals = W.index_payload(n)
+    need = R.radsort_workspace_size(n, 4, 4, 8, block_size=512, num_chunks=3)
+    ws = torch.empty(need, dtype=torch.uint8, device=DEV)
+    kt, vt = to_dev(keys), to_dev(vals)
+    R.sort_tensors(kt, vt, block_size=512, num_chunks=3, workspace=ws)
+    R.radsort_device_status()
+    ek, ev = oracle_sort(keys, vals, 32, 8)
+    assert np.array_equal(from_dev(kt, np.uint32), ek) and np.array_equal(from_dev(vt, np.uint32), ev)
+    small = torch.empty(need - 256, dtype=torch.uint8, device=DEV)
+    with pytest.raises(R.RadsortError):
+        R.sort_tensors(kt, vt, block_size=512, num_chunks=3, workspace=small)
+    for m in (0, 1):
+        t = torch.zeros(m, dtype=torch.int32, device=DEV)
+        R.sort_tensors(t, None)
+
+
+@pytest.mark.parametrize("kb,db", [(4, 8), (4, 11), (8, 8), (8, 11)])
+def test_lsd_oop_comparator(kb, db):
+    n = 300007
+    keys = W.make_keys("uniform", n, 8 * kb)
+    keys[::7] = keys[2]
+    vals = W.index_payload(n)
+    kt, vt = to_dev(keys), to_dev(vals)
+    ka, va = torch.empty_like(kt), torch.empty_like(vt)
+    R.lsd_oop_tensors(kt, vt, ka, va, digit_bits=db)
+    R.radsort_device_status()
+    lk, lv = oracle.lsd_oop(keys, vals, n_t=oracle.digits_for(8 * kb, db), sigma=1 << db, bits=db)
+    assert np.array_equal(from_dev(kt, keys.dtype), lk.astype(keys.dtype))
+    assert np.array_equal(from_dev(vt, np.uint32), lv)
+
+
+def check_sorted_stable_perm(orig_keys_t, keys_t, vals_t, key_bits):
+    """Properties that fix the unique stable sort at any size: the payload is a
+    permutation, keys[i] = orig[payload[i]], keys ascending, and equal keys
+    keep increasing payloads."""
+    n = keys_t.numel()
+    mask = (1 << key_bits) - 1
+    v = vals_t.to(torch.int64) & 0xFFFFFFFF
+    assert torch.equal(torch.sort(v).values, torch.arange(n, device=keys_t.device))
+    assert torch.equal(orig_keys_t[v], keys_t)
+    if key_bits == 32:
+        k = keys_t.to(torch.int64) & mask
+        assert bool((k[1:] >= k[:-1]).all())
+        eq = k[1:] == k[:-1]
+    else:  # compare 64-bit unsigned via the sign-flipped signed view
+        k = keys_t ^ (-(2 ** 63))
+        assert bool((k[1:] >= k[:-1]).all())
+        eq = keys_t[1:] == keys_t[:-1]
+    assert bool((v[1:][eq] > v[:-1][eq]).all())
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "equal", "sorted", "reverse"])
+def test_full_size_2p28_properties(dist):
+    """n = 2^28 uint32 keys + index payload, automatic plan (the bench's launch
+    configuration)."""
+    n = 1 << 28
+    keys = torch.from_numpy(W.make_keys(dist, n).view(np.int32)).to(DEV)
+    vals = torch.arange(n, dtype=torch.int32, device=DEV)
+    kt = keys.clone()
+    R.sort_tensors(kt, vals)
+    R.radsort_device_status()
+    check_sorted_stable_perm(keys, kt, vals, 32)
+    # sampled outputs the oracle computes one by one: rank of sampled keys
+    host = W.make_keys(dist, n)
+    for idx in (0, n // 3, n - 1):
+        pos = int((vals == idx).nonzero()[0, 0])
+        k = host[idx]
+        assert pos == int((host < k).sum()) + int((host[:idx] == k).sum())
