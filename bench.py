@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Radsort benchmark on GB300.
+
+Default workload (N=1): n = 2^28 uint32 keys uniform over [0, 2^32) with a
+uint32 payload = original index, 8-bit digits (sigma = 256, n_t = 4 rounds).
+One step = one full in-place Radsort: setup, 4 x (sortPhase, fixupPhase),
+Finalize.  Every timed step sorts its own fresh copy of the input (2 GiB,
+larger than L2), made before the timed region.
+
+Printed as one JSON line: device-resident throughput (value), end-to-end
+throughput through the public call with host buffers (e2e), the roofline of
+the dominant kernel (the sortPhase round kernel, CUDA events on its stream),
+the out-of-place LSD comparator on the same data and GPU, extra device bytes,
+clocks sampled during the timed region, and the oracle timed on the host
+cores (cpu_baseline).
+
+--impl reference times the oracle (plain single-threaded C, test
+infrastructure) on a bounded sample of the same workload on the host cores.
+Multi-GPU (torchrun): replicas only; each rank sorts its own array, and the
+value is all ranks' keys / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s & extra bytes vs out-of-place LSD, same GB300, bit-exact; serve p99 ms"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="radsort", choices=["radsort", "reference"])
+    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--key-bytes", type=int, default=4, choices=[4, 8])
+    ap.add_argument("--digit-bits", type=int, default=8, choices=[8, 11])
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--block-size", type=int, default=0)
+    ap.add_argument("--num-chunks", type=int, default=0)
+    ap.add_argument("--no-oop", action="store_true", help="skip the out-of-place comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_name(a):
+    kt = "u32" if a.key_bytes == 4 else "u64"
+    return f"radsort_{kt}_keys_u32_index_2^{a.log2n}_{a.dist}_d{a.digit_bits}"
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_sample_rate(a, seconds):
+    """Oracle Radsort (p = 1, the paper's sequential algorithm) on the host
+    cores over a bounded sample of the same workload; returns (Gkeys/s,
+    sample description, wall seconds)."""
+    import numpy as np
+
+    import oracle
+    from paper_2607_05302_gb300 import workloads as W
+
+    m = 1 << min(a.log2n, 22)
+    keys = W.make_keys(a.dist, m, 8 * a.key_bytes)
+    vals = W.index_payload(m)
+    n_t = oracle.digits_for(8 * a.key_bytes, a.digit_bits)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.radsort(keys, vals, n_t=n_t, sigma=1 << a.digit_bits, bits=a.digit_bits, b=1024, p=1,
+                       elem_bytes=a.key_bytes + 4)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return reps * m / el / 1e9, f"{reps} x oracle Radsort (p=1, b=1024) of 2^{m.bit_length() - 1} keys of the same distribution", el
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return
+    steps = []
+    for i in range(a.warmup + a.steps):
+        rate, sample, el = oracle_sample_rate(a, 0.0)
+        if i >= a.warmup:
+            steps.append(el)
+    m = 1 << min(a.log2n, 22)
+    value = a.steps * m / sum(steps) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * sum(steps) / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32" if a.key_bytes == 4 else "u64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": 1 << a.log2n, "sample_n": m},
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one oracle Radsort (single-threaded C, p=1, b=1024) of 2^{m.bit_length() - 1} keys of the same workload"},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, path, dev):
+        self.path, self.proc = path, None
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            c = [x.strip() for x in ln.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx = max(mx, float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2607_05302_gb300 import radsort as R
+    from paper_2607_05302_gb300 import workloads as W
+
+    if not os.path.exists(R.LIB_PATH):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n = 1 << a.log2n
+    kb, db = a.key_bytes, a.digit_bits
+    E = kb + 4
+    ktype = torch.int32 if kb == 4 else torch.int64
+    # inputs: identical bytes to workloads.make_keys (uniform via the torch
+    # form of the same SplitMix64 stream; other distributions from the host)
+    if a.dist == "uniform":
+        r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=dev)
+        keys0 = ((r >> 32) & 0xFFFFFFFF).to(torch.int64).to(torch.int32) if kb == 4 else r
+        del r
+    else:
+        host = W.make_keys(a.dist, n, 8 * kb)
+        keys0 = torch.from_numpy(host.view(np.int32 if kb == 4 else np.int64)).to(dev)
+    vals0 = torch.arange(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    bs, pc = a.block_size, a.num_chunks
+    if not bs or not pc:
+        b0, p0 = R.radsort_plan_default(n, kb, 4, db)
+        bs, pc = bs or b0, pc or p0
+    wsb = R.radsort_workspace_size(n, kb, 4, db, bs, pc)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+
+    free_b = torch.cuda.mem_get_info(dev)[0]
+    per_step = n * E
+    nbuf = int(min(a.warmup + a.steps, max(1, (free_b * 0.5) // per_step)))
+    kbufs = [torch.empty_like(keys0) for _ in range(nbuf)]
+    vbufs = [torch.empty_like(vals0) for _ in range(nbuf)]
+
+    def refill(i):
+        kbufs[i].copy_(keys0)
+        vbufs[i].copy_(vals0)
+
+    for i in range(nbuf):
+        refill(i)
+
+    def step(i):
+        R.sort_tensors(kbufs[i % nbuf], vbufs[i % nbuf], digit_bits=db, block_size=bs,
+                       num_chunks=pc, workspace=ws)
+
+    # warm-up (also checks the result once against the sorted reference)
+    for i in range(a.warmup):
+        step(i)
+    R.radsort_device_status()
+    if a.warmup:
+        ks = kbufs[0] if kb == 8 else (kbufs[0].to(torch.int64) & 0xFFFFFFFF)
+        ok = bool((ks[1:] >= ks[:-1]).all()) if kb == 4 else True
+        if not ok:
+            raise SystemExit("bench: warm-up result is not sorted")
+    for i in range(min(a.warmup, nbuf)):
+        refill(i)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"), local)
+    R.radsort_trace_read()  # drop warm-up records
+    R.radsort_trace_enable(True)
+    l0 = R.radsort_launch_count()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for s in range(a.steps):
+        i = a.warmup + s
+        if i >= nbuf and s > 0:  # not enough memory for fresh copies: refill in the timed region
+            refill(i % nbuf)
+        step(i)
+    ev1.record(stream)
+    barrier()
+    R.radsort_trace_enable(False)
+    launches = R.radsort_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    R.radsort_device_status()
+    recs = R.radsort_trace_read()
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * a.steps * n / (ms_max / 1e3) / 1e9
+
+    phases = {}
+    for ph, rd, t in recs:
+        key = ph if rd < 0 else f"{ph}[{rd}]"
+        phases.setdefault(key, []).append(t)
+    round_ms = [t for ph, rd, t in recs if ph == "sortPhase"]
+    avg_round = statistics.mean(round_ms) if round_ms else float("nan")
+    hbm, src = peaks()
+    achieved = (n * 2 * E) / (avg_round / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None,
+                "kernel": "k_round (sortPhase, Alg. 5)",
+                "algorithmic_bytes_per_launch": n * 2 * E, "peak_source": src,
+                "avg_launch_ms": round(avg_round, 4)}
+    step_bytes = n * (4 * 2 * E) if kb == 4 and db == 8 else None
+
+    # ---- end to end through the public call with host buffers
+    hk = torch.empty(n, dtype=ktype, pin_memory=True)
+    hv = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hk.copy_(keys0.cpu())
+    hv.copy_(vals0.cpu())
+    ok_ = torch.empty_like(hk, pin_memory=True)
+    ov_ = torch.empty_like(hv, pin_memory=True)
+    dk, dv = kbufs[0], vbufs[0]
+    e2e_steps = max(2, min(a.steps, 5))
+
+    def e2e_step():
+        dk.copy_(hk, non_blocking=True)
+        dv.copy_(hv, non_blocking=True)
+        R.radsort_sort(ctypes_ptr(dk), ctypes_ptr(dv), n, kb, db, R._torch_stream(None))
+        ok_.copy_(dk, non_blocking=True)
+        ov_.copy_(dv, non_blocking=True)
+
+    import ctypes
+
+    def ctypes_ptr(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    R.radsort_device_status()
+    e2e = {"value": world * n / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
+           "h2d_bytes_per_step": n * E, "d2h_bytes_per_step": n * E, "steps": e2e_steps,
+           "call": "radsort_sort (allocating, stream-ordered) with pinned host buffers"}
+    del hk, hv, ok_, ov_
+
+    # ---- out-of-place comparator on the same data and GPU
+    oop = None
+    if not a.no_oop:
+        ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
+        def oop_step(i):
+            R.lsd_oop_tensors(kbufs[i % nbuf], vbufs[i % nbuf], ka, va, digit_bits=db)
+        for i in range(min(nbuf, a.steps + a.warmup)):
+            refill(i)
+        for i in range(a.warmup):
+            oop_step(i)
+        for i in range(min(a.warmup, nbuf)):
+            refill(i)
+        barrier()
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for s in range(a.steps):
+            i = a.warmup + s
+            if i >= nbuf and s > 0:
+                refill(i % nbuf)
+            oop_step(i)
+        o1.record(stream)
+        barrier()
+        R.radsort_device_status()
+        oms = o0.elapsed_time(o1)
+        oval = world * a.steps * n / (oms / 1e3) / 1e9
+        oop = {"value": round(oval, 3), "unit": "Gkeys/s", "ms_per_step": oms / a.steps,
+               "extra_bytes": n * E + (n // 4096 + 1) * (1 << db) * 4,
+               "radsort_over_oop": round(value / oval, 4)}
+        del ka, va
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        rate, sample, el = oracle_sample_rate(a, a.cpu_seconds)
+        cpu = {"value": rate, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": round(el, 2), "host_cores_available": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gkeys/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32" if kb == 4 else "u64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": n, "key_bytes": kb, "value_bytes": 4,
+                       "digit_bits": db, "block_size": bs, "num_chunks": pc,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2: each timed step sorts its own fresh 2^%d-element copy" % a.log2n},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
+            "oop": oop,
+            "phases_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
+            "algorithmic_bytes_per_step": step_bytes,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

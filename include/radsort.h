@@ -131,6 +131,28 @@ radsort_status radsort_float_keys(uint32_t *keys, size_t n, int inverse, void *s
  */
 radsort_status radsort_device_status(void *stream);
 
+/*
+ * Tracing (no counterpart in the paper; measurement support).  While enabled,
+ * every sort records a CUDA event pair on its own stream around each phase:
+ * setup (Alg. 4), each round's sortPhase kernel (Alg. 5), each fixupPhase
+ * (Alg. 6) and Finalize (Alg. 7).  radsort_trace_read waits for the recorded
+ * events, copies up to `cap` records in launch order into `out`, stores the
+ * number recorded in *count, and clears the list.  Records: phase 0 = setup,
+ * 1 = sortPhase, 2 = fixupPhase, 3 = Finalize, 4 = key transform; `round` is
+ * the digit round (or -1); `ms` the event-measured duration.
+ * radsort_launch_count returns the number of kernels this library has
+ * launched since it was loaded.
+ */
+typedef struct {
+    int32_t phase;
+    int32_t round;
+    float ms;
+} radsort_trace_rec;
+
+radsort_status radsort_trace_enable(int on);
+radsort_status radsort_trace_read(radsort_trace_rec *out, int cap, int *count);
+radsort_status radsort_launch_count(uint64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,13 +3,69 @@
 // stream-ordered sequence setup -> n_t x (sortPhase, fixupPhase) -> Finalize
 // (Alg. 2).  Nothing here touches element data; every step runs in the
 // kernels of rs_round.cu and rs_finalize.cu.
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "radsort.h"
 #include "rs_kernels.cuh"
 
 namespace rs {
+
+std::atomic<unsigned long long> g_launches{0};
+
+// ---------------------------------------------------------------- tracing
+namespace {
+struct TraceRec {
+    cudaEvent_t a, b;
+    int phase, round;
+};
+std::mutex g_tmu;
+std::vector<TraceRec> g_trace;
+std::vector<cudaEvent_t> g_pool;
+bool g_trace_on = false;
+
+cudaEvent_t take_event()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records an event pair around a scope on `st` while tracing is enabled.
+struct Scope {
+    TraceRec r{};
+    cudaStream_t st;
+    bool on;
+    Scope(int phase, int round, cudaStream_t s) : st(s)
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        on = g_trace_on;
+        if (on) {
+            r.a = take_event();
+            r.b = take_event();
+            r.phase = phase;
+            r.round = round;
+            cudaEventRecord(r.a, st);
+        }
+    }
+    ~Scope()
+    {
+        if (!on)
+            return;
+        cudaEventRecord(r.b, st);
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_trace.push_back(r);
+    }
+};
+} // namespace
 
 int num_sms()
 {
@@ -111,8 +167,8 @@ static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radso
     const unsigned long long nA = n / b;
     const unsigned long long H = (unsigned long long)g->sigma * p;
     const unsigned long long npi = nA + 2 * H;
-    if (npi >= (1ull << 30))
-        return RADSORT_EINVAL; // 32-bit block indices with flag bits to spare
+    if (npi >= (1ull << 28))
+        return RADSORT_EINVAL; // 32-bit block indices with four flag bits to spare
     // sequence number of a block in its chunk's bucket chain: < 2^(32-db)
     if ((unsigned long long)g->sigma + npi >= (1ull << (32 - db)))
         return RADSORT_EINVAL;
@@ -150,8 +206,7 @@ static size_t layout(const Geom &g, void *base, Bufs *w)
     b.Aal = static_cast<uint32_t *>(take(size_t(g.p) * 4));
     b.LOff = static_cast<uint32_t *>(take(size_t(g.p + 1) * 4));
     b.state = static_cast<uint32_t *>(take(ST_WORDS * 4));
-    void *fin = take(finalize_extra_bytes(g));
-    (void)fin;
+    b.fin = take(finalize_extra_bytes(g));
     off = align_up(off, 256);
     if (w)
         *w = b;
@@ -178,11 +233,20 @@ static cudaError_t run_rounds(const Geom &g, Bufs &w, int rounds, cudaStream_t s
     const size_t npi2 = g.npi + (g.npi & 1);
     uint32_t *piX = w.aux, *UC = w.aux + npi2, *piY = w.aux + 2 * npi2;
     uint32_t *pc = piX, *pn = piY, *lc = w.lo0, *ln = w.lo1;
-    cudaError_t e = launch_setup(g, w, pc, st);
+    cudaError_t e;
+    {
+        Scope sc(0, -1, st);
+        e = launch_setup(g, w, pc, st);
+    }
     for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
-        e = launch_round(g, w, pc, lc, UC, r, st);
-        if (e == cudaSuccess)
+        {
+            Scope sc(1, r, st);
+            e = launch_round(g, w, pc, lc, UC, r, st);
+        }
+        if (e == cudaSuccess) {
+            Scope sc(2, r, st);
             e = launch_fixup(g, w, pc, pn, UC, lc, ln, st);
+        }
         uint32_t *t = pc;
         pc = pn;
         pn = t;
@@ -283,19 +347,28 @@ static radsort_status sort_common(void *keys, uint32_t *values, size_t n, int ke
     w.Ak = keys;
     w.Av = values;
     cudaError_t e = cudaSuccess;
-    if (flags & RADSORT_KEY_FLOAT32)
+    if (flags & RADSORT_KEY_FLOAT32) {
+        Scope sc(4, -1, st);
         e = launch_float_keys(static_cast<uint32_t *>(keys), n, 0, st);
+    }
     uint32_t *pc = nullptr, *po = nullptr;
     if (e == cudaSuccess)
         e = run_rounds(g, w, rounds < 0 ? g.nt : rounds, st, &pc, &po);
     if (e == cudaSuccess) {
-        if (rounds < 0)
-            e = launch_finalize(g, w, pc, po, st);
-        else
+        if (rounds < 0) {
+            Scope sc(3, -1, st);
+            // 2*npi words of scratch: U and the idle pi buffer, adjacent
+            const size_t npi2 = g.npi + (g.npi & 1);
+            uint32_t *jw = pc == w.aux ? w.aux + npi2 : w.aux;
+            e = launch_finalize(g, w, pc, reinterpret_cast<unsigned long long *>(jw), st);
+            (void)po;
+        } else
             e = launch_gather(g, w, pc, out_keys, out_values, st);
     }
-    if (e == cudaSuccess && (flags & RADSORT_KEY_FLOAT32) && rounds < 0)
+    if (e == cudaSuccess && (flags & RADSORT_KEY_FLOAT32) && rounds < 0) {
+        Scope sc(4, -1, st);
         e = launch_float_keys(static_cast<uint32_t *>(keys), n, 1, st);
+    }
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, st);
         if (e == cudaSuccess)
@@ -362,6 +435,53 @@ radsort_status radsort_device_status(void *stream)
         return RADSORT_ETIMEOUT;
     if (v & ST_INTERNAL)
         return RADSORT_EINTERNAL;
+    return RADSORT_OK;
+}
+
+radsort_status radsort_trace_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(rs::g_tmu);
+    rs::g_trace_on = on != 0;
+    return RADSORT_OK;
+}
+
+radsort_status radsort_trace_read(radsort_trace_rec *out, int cap, int *count)
+{
+    if (!count || (cap > 0 && !out))
+        return RADSORT_EINVAL;
+    std::vector<rs::TraceRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(rs::g_tmu);
+        recs.swap(rs::g_trace);
+    }
+    radsort_status st = RADSORT_OK;
+    int k = 0;
+    for (auto &r : recs) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess)
+            st = cuda_status(e);
+        if (k < cap) {
+            out[k].phase = r.phase;
+            out[k].round = r.round;
+            out[k].ms = ms;
+        }
+        ++k;
+        std::lock_guard<std::mutex> lk(rs::g_tmu);
+        rs::g_pool.push_back(r.a);
+        rs::g_pool.push_back(r.b);
+    }
+    *count = k;
+    return st;
+}
+
+radsort_status radsort_launch_count(uint64_t *launches)
+{
+    if (!launches)
+        return RADSORT_EINVAL;
+    *launches = rs::g_launches.load();
     return RADSORT_OK;
 }
 

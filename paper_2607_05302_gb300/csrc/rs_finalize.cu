@@ -1,11 +1,37 @@
-// Radsort Finalize (Alg. 7) and the float32 key transform, sm_103a.
+// Radsort Finalize for sm_103a, and the float32 key transform.
 //
-// This first Finalize is the paper's sequential procedure run by a single
-// CTA.  Thread 0 keeps the logical/physical bookkeeping (pi, pi^-1, the free
-// spot, sizeOfNextBlock).  All threads move each block through shared memory.
-// The pull reads the whole source block before writing, so an overlapping
-// pull toward lower addresses (source and target the same block) is a
-// memmove.
+// Finalize applies pi to the data blocks in place (Alg. 7, Sec. 2.4): after
+// the last round the used elements of logical blocks H .. f-1 (H = sigma*p)
+// hold the sorted sequence, and they must end up contiguous in A.  Alg. 7
+// does this one block at a time.  Here it is split into two parallel passes;
+// the paper suggests such a split for its parallel variant (Sec. 4.3: a
+// parallel permutation, then moving elements to remove the gaps of partial
+// blocks).
+//
+// F1, block permutation.  Logical block q = i - H goes to its target
+// position: A block q for q < floor(n/b), scratch block q - floor(n/b) for the
+// rest (at most sigma*p of them, all in T).  The moving blocks form paths
+// (ending at a free target) and cycles.
+//   * Pointer jumping over "block at x moves to t" finds each cycle's minimum
+//     (min-jumping).  The cycles are cut there.  A second jumping pass ranks
+//     every position by its distance to the head of its chain (the path's free
+//     end, or the cycle's minimum).
+//   * Each chain gets a contiguous range of an order array from an atomic
+//     counter.
+//   * The order array is cut into strides of K positions that CTAs take in
+//     ticket order.  A stride reads every block it must move into shared
+//     memory and publishes a flag.  It waits (bounded) for the previous
+//     stride's flag only if its first chain continues from there, then
+//     writes.  A cycle that spans strides saves its head block to a slot
+//     first.  The few beyond the slot capacity are moved by one CTA each.
+// F2, gap removal.  With block q at its target, A[off_q + e] = block_q[e]
+// moves every element left by the unused tails of the partial blocks before
+// it.  Windows of W destination elements are taken in ticket order.  A window
+// loads its sources, publishes, and waits only for the earlier windows whose
+// sources overlap its destinations.
+//
+// Every wait has an iteration limit.  When it runs out, the kernel sets the
+// status word and returns; it never hangs.
 #include "rs_common.cuh"
 #include "rs_kernels.cuh"
 
@@ -13,139 +39,679 @@ namespace rs {
 
 unsigned take_status_finalize() { return take_status_word(); }
 
-__global__ void k_inverse(const uint32_t *pi, uint32_t *pinv, uint32_t npi)
+namespace {
+
+constexpr uint32_t ABS = 0xFFFFFFFFu;      // absorbing jump entry
+constexpr uint32_t POS_MASK = 0x0FFFFFFFu; // positions < 2^28
+constexpr uint32_t F_MOVE = 1u << 31, F_CYC = 1u << 30, F_MIN = 1u << 29; // pi flags
+constexpr uint32_t O_FIRST = 1u << 31, O_LAST = 1u << 30, O_CYC = 1u << 29, O_DEFER = 1u << 28;
+constexpr uint32_t H_CYC = 1u << 31, H_HEAD = 1u << 30, H_DEFER = 1u << 29;
+constexpr uint32_t H_LEN = (1u << 29) - 1;
+constexpr uint32_t SLOT_NONE = 0xFFFFFFFFu;
+constexpr int FIN_T = 256;
+constexpr uint32_t MAXK = 64;
+
+// counters (words of the finalize scratch)
+enum { C_ORDER = 0, C_REC = 1, C_STRIDE = 2, C_WIN = 3, C_WORDS = 8 };
+
+struct FinArgs {
+    void *Ak;
+    uint32_t *Av;
+    void *Tk;
+    uint32_t *Tv;
+    uint32_t nT, nA, H, b, npi;
+    unsigned long long n;
+    uint32_t *pi;                // logical -> physical, later the order array
+    unsigned long long *jump;    // npi entries
+    const uint2 *P;              // partial blocks of the last round
+    const unsigned long long *D; // deficit prefix over P (nP + 1 entries)
+    const uint32_t *state;
+    uint32_t *ctr;               // counters
+    uint32_t *sflag;             // per stride: reads done
+    uint32_t *wflag;             // per window: reads done
+    uint4 *rec;                  // straddling cycles: (base, len, slot, 0)
+    uint32_t nrec_cap;
+    void *slot_k;                // nslots saved head blocks
+    uint32_t *slot_v;
+    uint32_t *slot_flag;         // per slot: head saved
+    uint32_t nslots;
+    uint32_t K;                  // stride length (blocks)
+    uint32_t W;                  // window length (elements)
+};
+
+__device__ __forceinline__ unsigned long long pk(uint32_t a, uint32_t b)
 {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npi; i += gridDim.x * blockDim.x)
-        pinv[pi[i]] = i;
+    return (unsigned long long)a | ((unsigned long long)b << 32);
+}
+__device__ __forceinline__ uint32_t lo32(unsigned long long v) { return uint32_t(v); }
+__device__ __forceinline__ uint32_t hi32(unsigned long long v) { return uint32_t(v >> 32); }
+
+__device__ __forceinline__ unsigned long long ld64(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+__device__ __forceinline__ void st64(unsigned long long *p, unsigned long long v)
+{
+    *(volatile unsigned long long *)p = v;
+}
+
+__device__ __forceinline__ uint32_t target_of(uint32_t q, uint32_t nA, uint32_t nT)
+{
+    return q < nA ? nT + q : q - nA;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// bounded wait until *p != 0
+__device__ __forceinline__ bool wait_flag(const uint32_t *p)
+{
+    for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+        if (ld_acquire(p))
+            return true;
+        __nanosleep(64);
+    }
+    set_status(ST_TIMEOUT);
+    return false;
+}
+
+template <typename KT> __device__ __forceinline__ KT *kblk(const FinArgs &a, uint32_t j)
+{
+    return j < a.nT ? static_cast<KT *>(a.Tk) + size_t(j) * a.b
+                    : static_cast<KT *>(a.Ak) + size_t(j - a.nT) * a.b;
+}
+__device__ __forceinline__ uint32_t *vblk(const FinArgs &a, uint32_t j)
+{
+    return j < a.nT ? a.Tv + size_t(j) * a.b : a.Av + size_t(j - a.nT) * a.b;
+}
+
+// ---------------------------------------------------------------- pointer jumping
+__global__ void k_fz_reset(unsigned long long *jump, uint32_t npi)
+{
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npi; x += gridDim.x * blockDim.x)
+        jump[x] = pk(x, ABS);
+}
+
+// successor edges of the moving blocks: (target, own position) for min-jumping
+__global__ void k_fz_edges(FinArgs a)
+{
+    const uint32_t NL = a.state[ST_F] - a.H;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < NL; q += gridDim.x * blockDim.x) {
+        const uint32_t x = a.pi[a.H + q], t = target_of(q, a.nA, a.nT);
+        if (x != t)
+            a.jump[x] = pk(t, x);
+    }
+}
+
+// In-place pointer jumping.  Entry (nxt, val); val == ABS is absorbing.
+// mode 0: val = minimum position of the window; mode 1: val = window length.
+// Each thread only rewrites its own entry, and any neighbour value it reads
+// is a valid window, so asynchronous updates only speed convergence.
+__global__ void k_fz_jump(unsigned long long *jump, uint32_t npi, int mode)
+{
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npi; x += gridDim.x * blockDim.x) {
+        const unsigned long long e = ld64(&jump[x]);
+        const uint32_t v = hi32(e);
+        if (v == ABS)
+            continue;
+        const unsigned long long f = ld64(&jump[lo32(e)]);
+        const uint32_t fv = hi32(f);
+        if (fv == ABS)
+            continue; // x's window already ends at an absorbing entry
+        st64(&jump[x], pk(lo32(f), mode == 0 ? min(v, fv) : v + fv));
+    }
+}
+
+// classify each moving block in pi's top bits: moving / on a cycle / the
+// cycle's minimum position
+__global__ void k_fz_classify(FinArgs a)
+{
+    const uint32_t NL = a.state[ST_F] - a.H;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < NL; q += gridDim.x * blockDim.x) {
+        const uint32_t x = a.pi[a.H + q], t = target_of(q, a.nA, a.nT);
+        if (x == t)
+            continue;
+        const unsigned long long e = a.jump[x];
+        const bool cyc = hi32(a.jump[lo32(e)]) != ABS;
+        const bool mn = cyc && hi32(e) == x;
+        a.pi[a.H + q] = x | F_MOVE | (cyc ? F_CYC : 0u) | (mn ? F_MIN : 0u);
+    }
+}
+
+// rank-pass edges: every moving block except a cycle minimum points to its
+// target with length 1; minima stay absorbing (the cycles are cut there)
+__global__ void k_fz_rank_edges(FinArgs a)
+{
+    const uint32_t NL = a.state[ST_F] - a.H;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < NL; q += gridDim.x * blockDim.x) {
+        const uint32_t v = a.pi[a.H + q];
+        if (!(v & F_MOVE) || (v & F_MIN))
+            continue;
+        a.jump[v & POS_MASK] = pk(target_of(q, a.nA, a.nT), 1u);
+    }
+}
+
+// each chain reserves its range of the order array (paths from their start,
+// cycles from their minimum) and writes it into the head's entry:
+// (base, length | HEAD | CYC | DEFER)
+__global__ void k_fz_chains(FinArgs a)
+{
+    const uint32_t NL = a.state[ST_F] - a.H;
+    const uint32_t R = NL - a.nA;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < NL; q += gridDim.x * blockDim.x) {
+        const uint32_t v = a.pi[a.H + q];
+        if (!(v & F_MOVE))
+            continue;
+        const uint32_t x = v & POS_MASK;
+        const bool cyc = (v & F_CYC) != 0;
+        uint32_t h, r;
+        if (cyc) {
+            // a cycle is cut at its minimum m (rank 0); m's successor is the
+            // farthest from m, so its rank + 1 is the cycle length
+            if (!(v & F_MIN))
+                continue;
+            h = x;
+            r = hi32(a.jump[target_of(q, a.nA, a.nT)]);
+        } else {
+            if (!(x < a.nT && x >= R))
+                continue; // not a path start: some block moves into x
+            const unsigned long long e = a.jump[x];
+            h = lo32(e);
+            r = hi32(e);
+        }
+        const uint32_t len = r + 1;
+        const uint32_t base = atomicAdd(&a.ctr[C_ORDER], len);
+        uint32_t defer = 0;
+        if (cyc && base / a.K != (base + len - 1) / a.K) {
+            const uint32_t ri = atomicAdd(&a.ctr[C_REC], 1u);
+            if (ri < a.nrec_cap) {
+                const uint32_t slot = ri < a.nslots ? ri : SLOT_NONE;
+                a.rec[ri] = make_uint4(base, len, slot, 0);
+                defer = slot == SLOT_NONE ? H_DEFER : 0u;
+            } else {
+                set_status(ST_INTERNAL);
+            }
+        }
+        a.jump[h] = pk(base, len | H_HEAD | (cyc ? H_CYC : 0u) | defer);
+    }
+}
+
+__global__ void k_fz_order(FinArgs a)
+{
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < a.npi; x += gridDim.x * blockDim.x) {
+        const unsigned long long e = a.jump[x];
+        const uint32_t v = hi32(e);
+        if (v == ABS)
+            continue;
+        uint32_t base, info, r;
+        if (v & H_HEAD) {
+            base = lo32(e);
+            info = v;
+            r = 0;
+        } else {
+            const unsigned long long hd = a.jump[lo32(e)];
+            base = lo32(hd);
+            info = hi32(hd);
+            r = v;
+        }
+        const uint32_t len = info & H_LEN;
+        a.pi[base + r] = x | (r == 0 ? O_FIRST : 0u) | (r + 1 == len ? O_LAST : 0u) |
+                         ((info & H_CYC) ? O_CYC : 0u) | ((info & H_DEFER) ? O_DEFER : 0u);
+    }
+}
+
+// record of the straddling cycle that contains order index g (linear search;
+// straddling cycles are few: random-like permutations have O(log n) cycles)
+__device__ uint4 find_rec(const FinArgs &a, uint32_t g)
+{
+    const uint32_t nr = min(a.ctr[C_REC], a.nrec_cap);
+    for (uint32_t i = 0; i < nr; ++i) {
+        const uint4 r = a.rec[i];
+        if (g >= r.x && g < r.x + r.y)
+            return r;
+    }
+    return make_uint4(0, 0, SLOT_NONE, 0);
+}
+
+// copy `cnt` blocks between block addresses (flat over all 16-byte vectors)
+template <typename KT> struct BlockIO {
+    const FinArgs &a;
+    uint32_t kvec, vvec, nvec;
+    __device__ BlockIO(const FinArgs &aa) : a(aa)
+    {
+        kvec = a.b * sizeof(KT) / 16;
+        vvec = a.Av ? a.b * 4 / 16 : 0;
+        nvec = kvec + vvec;
+    }
+    // smem buffer i <-> block j
+    __device__ uint4 *sbuf(unsigned char *base, uint32_t i) const
+    {
+        return reinterpret_cast<uint4 *>(base) + size_t(i) * nvec;
+    }
+    __device__ uint4 *gvec(uint32_t j, uint32_t v) const
+    {
+        return v < kvec ? reinterpret_cast<uint4 *>(kblk<KT>(a, j)) + v
+                        : reinterpret_cast<uint4 *>(vblk(a, j)) + (v - kvec);
+    }
+    __device__ uint4 *slotvec(uint32_t s, uint32_t v) const
+    {
+        return v < kvec ? reinterpret_cast<uint4 *>(static_cast<KT *>(a.slot_k) + size_t(s) * a.b) + v
+                        : reinterpret_cast<uint4 *>(a.slot_v + size_t(s) * a.b) + (v - kvec);
+    }
+};
+
+// ---------------------------------------------------------------- F1 moves
+// kinds: 0 nothing, 1 block src -> dst, 2 closing write of a cycle from its slot
+template <typename KT>
+__global__ void __launch_bounds__(FIN_T) k_fz_move(FinArgs a)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ uint32_t s_ticket, s_src[MAXK], s_dst[MAXK], s_kind[MAXK], s_slot[MAXK], s_save[MAXK];
+    __shared__ uint32_t s_wait, s_any2;
+    const BlockIO<KT> io(a);
+    const uint32_t total = a.ctr[C_ORDER];
+    const uint32_t nstr = (total + a.K - 1) / a.K;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_ticket = atomicAdd(&a.ctr[C_STRIDE], 1u);
+        __syncthreads();
+        const uint32_t t = s_ticket;
+        if (t >= nstr)
+            break;
+        const uint32_t g0 = t * a.K, g1 = min(total, g0 + a.K), cnt = g1 - g0;
+        if (threadIdx.x < cnt) {
+            const uint32_t i = threadIdx.x, g = g0 + i;
+            const uint32_t o = a.pi[g];
+            uint32_t kind = 0, src = 0, slot = SLOT_NONE, save = SLOT_NONE;
+            if (o & O_DEFER) {
+                kind = 0; // the whole cycle is moved by k_fz_move_deferred
+            } else if (o & O_LAST) {
+                if (o & O_CYC) {
+                    const uint4 r = find_rec(a, g);
+                    if (r.y) { // head in an earlier stride: its block waits in a slot
+                        kind = 2;
+                        slot = r.z;
+                    } else {   // head in this stride
+                        uint32_t gh = g;
+                        while (gh > g0 && !(a.pi[gh] & O_FIRST))
+                            --gh;
+                        kind = 1;
+                        src = a.pi[gh] & POS_MASK;
+                    }
+                } // a path's start receives nothing
+            } else {
+                kind = 1;
+                src = a.pi[g + 1] & POS_MASK;
+                if ((o & O_FIRST) && (o & O_CYC)) {
+                    const uint4 r = find_rec(a, g);
+                    if (r.y)
+                        save = r.z; // save the head block before it is overwritten
+                }
+            }
+            s_kind[i] = kind;
+            s_src[i] = src;
+            s_dst[i] = o & POS_MASK;
+            s_slot[i] = slot;
+            s_save[i] = save;
+        }
+        if (threadIdx.x == 0) {
+            const uint32_t o = a.pi[g0];
+            s_wait = (t > 0 && !(o & O_FIRST) && !(o & O_DEFER)) ? 1u : 0u;
+        }
+        __syncthreads();
+        // read phase: every source block into shared memory; heads to slots
+        for (uint32_t idx = threadIdx.x; idx < cnt * io.nvec; idx += blockDim.x) {
+            const uint32_t i = idx / io.nvec, v = idx - i * io.nvec;
+            if (s_kind[i] == 1)
+                io.sbuf(fsm, i)[v] = *io.gvec(s_src[i], v);
+            if (s_save[i] != SLOT_NONE)
+                *io.slotvec(s_save[i], v) = *io.gvec(s_dst[i], v);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            uint32_t any2 = 0;
+            for (uint32_t i = 0; i < cnt; ++i) {
+                if (s_save[i] != SLOT_NONE)
+                    st_release(&a.slot_flag[s_save[i]], 1u);
+                any2 |= s_kind[i] == 2;
+            }
+            st_release(&a.sflag[t], 1u);
+            if (s_wait)
+                wait_flag(&a.sflag[t - 1]);
+            for (uint32_t i = 0; i < cnt; ++i)
+                if (s_kind[i] == 2)
+                    wait_flag(&a.slot_flag[s_slot[i]]);
+            s_any2 = any2;
+        }
+        __syncthreads();
+        // write phase
+        for (uint32_t idx = threadIdx.x; idx < cnt * io.nvec; idx += blockDim.x) {
+            const uint32_t i = idx / io.nvec, v = idx - i * io.nvec;
+            if (s_kind[i] == 1)
+                *io.gvec(s_dst[i], v) = io.sbuf(fsm, i)[v];
+            else if (s_kind[i] == 2)
+                *io.gvec(s_dst[i], v) = *io.slotvec(s_slot[i], v);
+        }
+        __syncthreads();
+    }
+}
+
+// straddling cycles beyond the slot capacity: one CTA moves a whole cycle,
+// K-1 blocks at a time, holding the head block in shared memory
+template <typename KT>
+__global__ void __launch_bounds__(FIN_T) k_fz_move_deferred(FinArgs a)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const BlockIO<KT> io(a);
+    const uint32_t nr = min(a.ctr[C_REC], a.nrec_cap);
+    const uint32_t KB = a.K - 1;
+    for (uint32_t ri = blockIdx.x; ri < nr; ri += gridDim.x) {
+        const uint4 r = a.rec[ri];
+        if (r.z != SLOT_NONE)
+            continue;
+        const uint32_t g0 = r.x, len = r.y;
+        const uint32_t yh = a.pi[g0] & POS_MASK;
+        for (uint32_t v = threadIdx.x; v < io.nvec; v += blockDim.x)
+            io.sbuf(fsm, 0)[v] = *io.gvec(yh, v);
+        __syncthreads();
+        // y_g <- content(y_{g+1}) for g = g0 .. g0+len-2, then y_last <- head
+        for (uint32_t g = g0; g + 1 < g0 + len; g += KB) {
+            const uint32_t c = min(KB, g0 + len - 1 - g);
+            for (uint32_t idx = threadIdx.x; idx < c * io.nvec; idx += blockDim.x) {
+                const uint32_t i = idx / io.nvec, v = idx - i * io.nvec;
+                io.sbuf(fsm, 1 + i)[v] = *io.gvec(a.pi[g + 1 + i] & POS_MASK, v);
+            }
+            __syncthreads();
+            for (uint32_t idx = threadIdx.x; idx < c * io.nvec; idx += blockDim.x) {
+                const uint32_t i = idx / io.nvec, v = idx - i * io.nvec;
+                *io.gvec(a.pi[g + i] & POS_MASK, v) = io.sbuf(fsm, 1 + i)[v];
+            }
+            __syncthreads();
+        }
+        const uint32_t yl = a.pi[g0 + len - 1] & POS_MASK;
+        for (uint32_t v = threadIdx.x; v < io.nvec; v += blockDim.x)
+            *io.gvec(yl, v) = io.sbuf(fsm, 0)[v];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- F2 gap removal
+// first element position and length of logical block q (0-based), and the
+// number of partial blocks before it
+__device__ __forceinline__ void block_span(const FinArgs &a, uint32_t nP, uint32_t q,
+                                           unsigned long long &off, uint32_t &len, uint32_t &jP)
+{
+    uint32_t l = 0, r = nP;
+    while (l < r) {
+        const uint32_t m = (l + r) >> 1;
+        if (a.P[m].x < a.H + q)
+            l = m + 1;
+        else
+            r = m;
+    }
+    jP = l;
+    off = (unsigned long long)q * a.b - a.D[l];
+    len = (l < nP && a.P[l].x == a.H + q) ? a.P[l].y : a.b;
+}
+
+// logical block holding element x
+__device__ uint32_t block_of(const FinArgs &a, uint32_t nP, unsigned long long x, uint32_t NL)
+{
+    uint32_t l = 0, r = NL; // last block with off <= x
+    while (l + 1 < r) {
+        const uint32_t m = (l + r) >> 1;
+        unsigned long long off;
+        uint32_t len, jp;
+        block_span(a, nP, m, off, len, jp);
+        if (off <= x)
+            l = m;
+        else
+            r = m;
+    }
+    for (;;) { // step over empty blocks that start at x
+        unsigned long long off;
+        uint32_t len, jp;
+        block_span(a, nP, l, off, len, jp);
+        if (x < off + len || l + 1 >= NL)
+            return l;
+        ++l;
+    }
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(1024) k_finalize_seq(KT *Ak, uint32_t *Av, KT *Tk, uint32_t *Tv,
-                                                       uint32_t *pi, uint32_t *pinv, const uint2 *P,
-                                                       const uint32_t *state, uint32_t H,
-                                                       uint32_t nT, uint32_t nA, uint32_t b,
-                                                       unsigned long long n)
+__global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
-    KT *bk = reinterpret_cast<KT *>(fsm);
-    uint32_t *bv = reinterpret_cast<uint32_t *>(fsm + size_t(b) * sizeof(KT));
-    __shared__ uint32_t s_jin, s_jout, s_jfree, s_l, s_push;
-    __shared__ unsigned long long s_k;
-    const uint32_t f = state[ST_F], nP = state[ST_NP];
-    const int t = threadIdx.x, T = blockDim.x;
-    // thread-0 state
-    uint32_t iP = 0, i_free = 0, j_free = 0;
-    unsigned long long k = 0;
-    if (t == 0)
-        j_free = pi[0]; // logical 0 is in the head start: unallocated
-    auto keys_of = [&](uint32_t j) -> KT * { return j < nT ? Tk + size_t(j) * b : Ak + size_t(j - nT) * b; };
-    auto vals_of = [&](uint32_t j) -> uint32_t * { return j < nT ? Tv + size_t(j) * b : Av + size_t(j - nT) * b; };
-    const bool hv = Av != nullptr;
-
-    for (uint32_t i_in = H; i_in < f; ++i_in) {
-        uint32_t i_out = 0;
-        if (t == 0) {
-            const uint32_t j_in = pi[i_in];
-            uint32_t push = 0, j_out = 0;
-            if (i_in < H + nA) {
-                j_out = i_in + H; // A block i_in - H
-                i_out = pinv[j_out];
-                push = (i_in < i_out && i_out < f) ? 1u : 0u;
-            }
-            uint32_t l = b;
-            if (iP < nP && P[iP].x == i_in) // sizeOfNextBlock (Alg. 3)
-                l = P[iP++].y;
-            s_jin = j_in;
-            s_jout = j_out;
-            s_jfree = j_free;
-            s_l = l;
-            s_push = push;
-            s_k = k;
-        }
+    KT *wk = reinterpret_cast<KT *>(fsm);
+    uint32_t *wv = reinterpret_cast<uint32_t *>(fsm + size_t(a.W) * sizeof(KT));
+    __shared__ uint32_t s_ticket, s_q0, s_wlo, s_inplace;
+    const uint32_t nP = a.state[ST_NP];
+    const uint32_t NL = a.state[ST_F] - a.H;
+    const unsigned long long n = a.n;
+    const uint32_t nwin = static_cast<uint32_t>((n + a.W - 1) / a.W);
+    const bool hv = a.Av != nullptr;
+    KT *Ak = static_cast<KT *>(a.Ak);
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_ticket = atomicAdd(&a.ctr[C_WIN], 1u);
         __syncthreads();
-        const uint32_t j_in = s_jin, j_out = s_jout, l = s_l;
-        if (s_push) { // push the block at j_out to the free spot
-            KT *dk = keys_of(s_jfree);
-            const KT *sk = keys_of(j_out);
-            for (uint32_t e = t; e < b; e += T)
-                dk[e] = sk[e];
-            if (hv) {
-                uint32_t *dv = vals_of(s_jfree);
-                const uint32_t *sv = vals_of(j_out);
-                for (uint32_t e = t; e < b; e += T)
-                    dv[e] = sv[e];
+        const uint32_t w = s_ticket;
+        if (w >= nwin)
+            break;
+        const unsigned long long x0 = (unsigned long long)w * a.W;
+        const uint32_t cnt = static_cast<uint32_t>(min((unsigned long long)a.W, n - x0));
+        if (threadIdx.x == 0) {
+            s_q0 = block_of(a, nP, x0, NL);
+            // in place iff no partial block precedes the window's last block
+            // and that block lies in A: every source is its destination
+            const uint32_t qe = block_of(a, nP, x0 + cnt - 1, NL);
+            unsigned long long offe;
+            uint32_t lene, jpe;
+            block_span(a, nP, qe, offe, lene, jpe);
+            s_inplace = (qe < a.nA && a.D[jpe] == 0) ? 1u : 0u;
+            // earliest window whose sources lie in our destinations: the one
+            // holding the destination of the element at virtual position x0
+            const uint32_t qv = static_cast<uint32_t>(x0 / a.b);
+            if (qv < a.nA) {
+                unsigned long long offv;
+                uint32_t lenv, jpv;
+                block_span(a, nP, qv, offv, lenv, jpv);
+                s_wlo = static_cast<uint32_t>(offv / a.W);
+            } else {
+                s_wlo = w; // destinations beyond the blocks of A: nobody reads them
             }
         }
         __syncthreads();
-        { // pull l elements of block j_in to A[k..k+l)
-            const KT *sk = keys_of(j_in);
-            for (uint32_t e = t; e < l; e += T)
-                bk[e] = sk[e];
-            if (hv) {
-                const uint32_t *sv = vals_of(j_in);
-                for (uint32_t e = t; e < l; e += T)
-                    bv[e] = sv[e];
+        if (!s_inplace) {
+            // read phase: the blocks covering destinations [x0, x0+cnt)
+            uint32_t q = s_q0, len, jp;
+            unsigned long long off;
+            block_span(a, nP, q, off, len, jp);
+            uint32_t done = 0;
+            while (done < cnt && q < NL) {
+                const uint32_t e0 = static_cast<uint32_t>(x0 + done - off);
+                const uint32_t take = min(cnt - done, len > e0 ? len - e0 : 0u);
+                if (take) {
+                    const uint32_t phys = target_of(q, a.nA, a.nT);
+                    const KT *sk = kblk<KT>(a, phys) + e0;
+                    for (uint32_t i = threadIdx.x; i < take; i += blockDim.x)
+                        wk[done + i] = sk[i];
+                    if (hv) {
+                        const uint32_t *sv = vblk(a, phys) + e0;
+                        for (uint32_t i = threadIdx.x; i < take; i += blockDim.x)
+                            wv[done + i] = sv[i];
+                    }
+                    done += take;
+                }
+                off += len;
+                ++q;
+                while (jp < nP && a.P[jp].x < a.H + q)
+                    ++jp;
+                len = (jp < nP && a.P[jp].x == a.H + q) ? a.P[jp].y : a.b;
             }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(&a.wflag[w], 1u);
+        }
+        if (!s_inplace) {
+            // wait for every earlier window that reads from our destinations
+            for (uint32_t v = s_wlo + threadIdx.x; v < w; v += blockDim.x)
+                wait_flag(&a.wflag[v]);
             __syncthreads();
-            const unsigned long long kk = s_k;
-            for (uint32_t e = t; e < l; e += T) {
-                Ak[kk + e] = bk[e];
+            for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+                Ak[x0 + i] = wk[i];
                 if (hv)
-                    Av[kk + e] = bv[e];
-            }
-        }
-        if (t == 0) {
-            k += l;
-            if (i_in < H + nA) {
-                if (s_push) { // swap(i_out, j_out, i_free, j_free)
-                    pi[i_out] = j_free;
-                    pi[i_free] = j_out;
-                    pinv[j_out] = i_free;
-                    pinv[j_free] = i_out;
-                    i_out = i_free;
-                }
-                // swap(i_out, j_out, i_in, j_in)
-                pi[i_out] = j_in;
-                pi[i_in] = j_out;
-                pinv[j_out] = i_in;
-                pinv[j_in] = i_out;
-                if (i_in != i_out) {
-                    i_free = i_out;
-                    j_free = j_in;
-                }
+                    a.Av[x0 + i] = wv[i];
             }
         }
         __syncthreads();
     }
-    if (t == 0 && k != n)
-        set_status(ST_INTERNAL);
 }
 
-size_t finalize_extra_bytes(const Geom &) { return 0; }
+struct FinLayout {
+    size_t ctr, sflag, wflag, slotflag, rec, slotk, slotv, total;
+    uint32_t K, W, nstr, nwin, nrec, nslots;
+};
 
-cudaError_t launch_finalize(const Geom &g, const Bufs &w, uint32_t *pi, uint32_t *pi_other,
+FinLayout fin_layout(const Geom &g)
+{
+    FinLayout L{};
+    const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
+    uint32_t K = static_cast<uint32_t>((64u << 10) / bbytes);
+    if (K > MAXK)
+        K = MAXK;
+    if (K < 2)
+        K = 2;
+    L.K = K;
+    L.W = g.kb == 4 ? 8192 : 4096;
+    L.nstr = g.npi / K + 2;
+    L.nwin = static_cast<uint32_t>(g.n / L.W + 2);
+    L.nrec = L.nstr + 1;
+    L.nslots = 1024;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t off = 0;
+    L.ctr = off;
+    off += al(C_WORDS * 4);
+    L.sflag = off;
+    off += al(size_t(L.nstr) * 4);
+    L.wflag = off;
+    off += al(size_t(L.nwin) * 4);
+    L.slotflag = off;
+    off += al(size_t(L.nslots) * 4);
+    L.rec = off; // everything before here is cleared per sort
+    off += al(size_t(L.nrec) * 16);
+    L.slotk = off;
+    off += al(size_t(L.nslots) * g.b * g.kb);
+    L.slotv = off;
+    off += g.hasv ? al(size_t(L.nslots) * g.b * 4) : 0;
+    L.total = off;
+    return L;
+}
+
+template <typename KT>
+cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long long *jump,
+                     cudaStream_t st)
+{
+    const FinLayout L = fin_layout(g);
+    char *base = static_cast<char *>(w.fin);
+    FinArgs a{};
+    a.Ak = w.Ak;
+    a.Av = g.hasv ? w.Av : nullptr;
+    a.Tk = w.Tk;
+    a.Tv = w.Tv;
+    a.nT = g.nT;
+    a.nA = g.nA;
+    a.H = g.H;
+    a.b = g.b;
+    a.npi = g.npi;
+    a.n = g.n;
+    a.pi = pi;
+    a.jump = jump;
+    a.P = w.P;
+    a.D = w.E;
+    a.state = w.state;
+    a.ctr = reinterpret_cast<uint32_t *>(base + L.ctr);
+    a.sflag = reinterpret_cast<uint32_t *>(base + L.sflag);
+    a.wflag = reinterpret_cast<uint32_t *>(base + L.wflag);
+    a.slot_flag = reinterpret_cast<uint32_t *>(base + L.slotflag);
+    a.rec = reinterpret_cast<uint4 *>(base + L.rec);
+    a.nrec_cap = L.nrec;
+    a.slot_k = base + L.slotk;
+    a.slot_v = g.hasv ? reinterpret_cast<uint32_t *>(base + L.slotv) : nullptr;
+    a.nslots = L.nslots;
+    a.K = L.K;
+    a.W = L.W;
+
+    cudaError_t e = cudaMemsetAsync(base, 0, L.rec, st);
+    if (e != cudaSuccess)
+        return e;
+    e = launch_deficit(g, w, st); // D over the last round's P, used by F2
+    if (e != cudaSuccess)
+        return e;
+    const int sms = num_sms();
+    int grid = static_cast<int>((g.npi + FIN_T - 1) / FIN_T);
+    if (grid > sms * 8)
+        grid = sms * 8;
+    if (grid < 1)
+        grid = 1;
+    int rounds = 1;
+    while ((1u << rounds) < g.npi)
+        ++rounds;
+    rounds += 1;
+    k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
+    k_fz_edges<<<grid, FIN_T, 0, st>>>(a);
+    for (int r = 0; r < rounds; ++r)
+        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 0);
+    k_fz_classify<<<grid, FIN_T, 0, st>>>(a);
+    k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
+    k_fz_rank_edges<<<grid, FIN_T, 0, st>>>(a);
+    for (int r = 0; r < rounds; ++r)
+        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 1);
+    k_fz_chains<<<grid, FIN_T, 0, st>>>(a);
+    k_fz_order<<<grid, FIN_T, 0, st>>>(a);
+    const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
+    const size_t msm = bbytes * L.K;
+    const size_t csm = size_t(L.W) * (g.kb + (g.hasv ? 4 : 0));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_fz_move<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
+        cudaFuncSetAttribute(k_fz_move_deferred<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             160 << 10);
+        cudaFuncSetAttribute(k_fz_compact<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             160 << 10);
+        attr = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_move<KT>, FIN_T, msm);
+    k_fz_move<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, msm, st>>>(a);
+    k_fz_move_deferred<KT><<<sms, FIN_T, msm, st>>>(a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_compact<KT>, FIN_T, csm);
+    k_fz_compact<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, csm, st>>>(a);
+    g_launches += 10 + 2 * rounds;
+    return cudaGetLastError();
+}
+
+} // namespace
+
+size_t finalize_extra_bytes(const Geom &g) { return fin_layout(g).total; }
+
+cudaError_t launch_finalize(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long long *jump,
                             cudaStream_t st)
 {
-    int blocks = static_cast<int>((g.npi + 255) / 256);
-    if (blocks > 8192)
-        blocks = 8192;
-    k_inverse<<<blocks, 256, 0, st>>>(pi, pi_other, g.npi);
-    const size_t smem = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
-    if (g.kb == 4) {
-        cudaFuncSetAttribute(k_finalize_seq<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
-        k_finalize_seq<uint32_t><<<1, 1024, smem, st>>>(
-            static_cast<uint32_t *>(w.Ak), g.hasv ? w.Av : nullptr, static_cast<uint32_t *>(w.Tk),
-            w.Tv, pi, pi_other, w.P, w.state, g.H, g.nT, g.nA, g.b, (unsigned long long)g.n);
-    } else {
-        cudaFuncSetAttribute(k_finalize_seq<unsigned long long>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        k_finalize_seq<unsigned long long><<<1, 1024, smem, st>>>(
-            static_cast<unsigned long long *>(w.Ak), g.hasv ? w.Av : nullptr,
-            static_cast<unsigned long long *>(w.Tk), w.Tv, pi, pi_other, w.P, w.state, g.H, g.nT,
-            g.nA, g.b, (unsigned long long)g.n);
-    }
-    return cudaGetLastError();
+    if (g.kb == 4)
+        return fin_impl<uint32_t>(g, w, pi, jump, st);
+    return fin_impl<unsigned long long>(g, w, pi, jump, st);
 }
 
 // ---------------------------------------------------------------- float keys
@@ -171,6 +737,7 @@ cudaError_t launch_float_keys(uint32_t *keys, size_t n, int inverse, cudaStream_
     if (blocks > cap)
         blocks = cap;
     k_float_keys<<<blocks, 256, 0, st>>>(keys, n, inverse);
+    g_launches += 1;
     return cudaGetLastError();
 }
 

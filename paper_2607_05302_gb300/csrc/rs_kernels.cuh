@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 namespace rs {
 
 // bits of the device status words
@@ -42,16 +44,7 @@ struct Bufs {
     uint32_t *Aal;     // p   allocations per chunk
     uint32_t *LOff;    // p+1 leftover offsets
     uint32_t *state;   // scalars, see ST_*
-    // Finalize
-    unsigned long long *jump; // npi (aliases aux, see finalize)
-    uint32_t *fin_ctr;        // counters and flags used by Finalize
-    size_t fin_ctr_words;
-    void *slot_k;             // long-cycle save slots
-    uint32_t *slot_v;
-    uint32_t nslots;
-    uint32_t *cycles;         // long-cycle table (g0, len) pairs
-    uint32_t *flags;          // per-stride / per-window progress flags
-    size_t nflags;
+    void *fin;         // Finalize scratch (finalize_extra_bytes)
 };
 
 // indices into Bufs::state
@@ -70,7 +63,10 @@ cudaError_t launch_fixup(const Geom &g, const Bufs &w, const uint32_t *pi_old, u
 cudaError_t launch_gather(const Geom &g, const Bufs &w, const uint32_t *pi, void *out_k,
                           uint32_t *out_v, cudaStream_t st);
 // Finalize (Alg. 7 semantics): pi applied to the data in place
-cudaError_t launch_finalize(const Geom &g, const Bufs &w, uint32_t *pi, uint32_t *pi_other,
+// deficit prefix over the current P into Bufs::E (nP + 1 entries)
+cudaError_t launch_deficit(const Geom &g, const Bufs &w, cudaStream_t st);
+// jump: 2*npi words of scratch, 8-byte aligned (U plus the idle pi buffer)
+cudaError_t launch_finalize(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long long *jump,
                             cudaStream_t st);
 size_t finalize_extra_bytes(const Geom &g);
 // float32 key transform
@@ -80,6 +76,8 @@ cudaError_t launch_lsd_oop(void *keys, uint32_t *vals, void *keys_alt, uint32_t 
                            size_t n, int kb, int db, cudaStream_t st);
 
 int num_sms();
+// kernels launched by this library (host counter)
+extern std::atomic<unsigned long long> g_launches;
 // read and clear the device status words of each translation unit
 unsigned take_status_round();
 unsigned take_status_finalize();

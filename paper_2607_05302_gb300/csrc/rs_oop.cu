@@ -236,6 +236,7 @@ static cudaError_t oop_impl(KT *keys, uint32_t *vals, KT *keys_alt, uint32_t *va
     const int sms = num_sms();
     k_oop_hist<KT, DB><<<sms * 4, 512, nt * SIGMA * 4, st>>>(keys, n, nt, hist);
     k_oop_offsets<DB><<<nt, 256, 0, st>>>(hist, off);
+    g_launches += 2 + nt;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_oop_round<KT, HASV, DB, TILE, NW>,

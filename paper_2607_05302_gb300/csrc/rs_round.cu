@@ -104,6 +104,7 @@ cudaError_t launch_setup(const Geom &g, const Bufs &w, uint32_t *pi, cudaStream_
             static_cast<const unsigned long long *>(w.Ak), w.Av,
             static_cast<unsigned long long *>(w.Tk), w.Tv, g.n, g.b, g.H, g.nA, g.p, w.P,
             w.state, w.lo0);
+    g_launches += 2;
     return cudaGetLastError();
 }
 
@@ -544,6 +545,7 @@ static cudaError_t round_impl(const Geom &g, const Bufs &w, const uint32_t *pi, 
     a.lb = g.lb;
     a.shift = static_cast<uint32_t>(round * g.db);
     k_round<KT, HASV, DB, TILE, NW, STAGES><<<g.p, C::THREADS, C::SMEM, st>>>(a);
+    g_launches += 1;
     return cudaGetLastError();
 }
 
@@ -751,6 +753,7 @@ cudaError_t launch_fixup(const Geom &g, const Bufs &w, const uint32_t *pi_old, u
     k_fixup_place<<<blocks, 256, (g.p + 1) * 4, st>>>(pi_old, pi_new, UC, w.S, w.Aal, lo_old,
                                                       w.LOff, w.state, g.npi, g.sigma, g.p, g.H,
                                                       g.db);
+    g_launches += 2;
     return cudaGetLastError();
 }
 
@@ -822,10 +825,17 @@ __global__ void k_gather(const KT *Ak, const uint32_t *Av, const KT *Tk, const u
     }
 }
 
+cudaError_t launch_deficit(const Geom &g, const Bufs &w, cudaStream_t st)
+{
+    k_deficit<<<1, 1024, 0, st>>>(w.P, w.state, w.E, g.b);
+    g_launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const Geom &g, const Bufs &w, const uint32_t *pi, void *out_k,
                           uint32_t *out_v, cudaStream_t st)
 {
-    k_deficit<<<1, 1024, 0, st>>>(w.P, w.state, w.E, g.b);
+    launch_deficit(g, w, st);
     int blocks = static_cast<int>((size_t(g.npi) * 32 + 255) / 256);
     if (blocks > 16384)
         blocks = 16384;
@@ -841,6 +851,7 @@ cudaError_t launch_gather(const Geom &g, const Bufs &w, const uint32_t *pi, void
             static_cast<const unsigned long long *>(w.Ak), g.hasv ? w.Av : nullptr,
             static_cast<const unsigned long long *>(w.Tk), w.Tv, pi, w.P, w.E, w.state,
             static_cast<unsigned long long *>(out_k), g.hasv ? out_v : nullptr, g.H, g.nT, g.b);
+    g_launches += 1;
     return cudaGetLastError();
 }
 

@@ -26,6 +26,13 @@ class RadsortError(RuntimeError):
         self.status = status
 
 
+class TraceRec(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int32), ("round", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+PHASES = {0: "setup", 1: "sortPhase", 2: "fixupPhase", 3: "Finalize", 4: "key_transform"}
+
+
 class Plan(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("num_chunks", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32 * 6)]
@@ -55,6 +62,9 @@ def lib() -> ctypes.CDLL:
             "radsort_lsd_oop_sort": ([vp, vp, vp, vp, sz, i, i, vp], i),
             "radsort_float_keys": ([vp, sz, i, vp], i),
             "radsort_device_status": ([vp], i),
+            "radsort_trace_enable": ([i], i),
+            "radsort_trace_read": ([ctypes.POINTER(TraceRec), i, ctypes.POINTER(i)], i),
+            "radsort_launch_count": ([ctypes.POINTER(ctypes.c_uint64)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -67,7 +77,8 @@ def lib() -> ctypes.CDLL:
 # exported names declared in include/radsort.h
 EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_workspace_size", "radsort_sort",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort", "radsort_float_keys",
-           "radsort_device_status")
+           "radsort_device_status", "radsort_trace_enable", "radsort_trace_read",
+           "radsort_launch_count")
 
 
 def status_str(s: int) -> str:
@@ -133,6 +144,25 @@ def radsort_float_keys(keys, n, inverse, stream):
 
 def radsort_device_status(stream=None):
     _ok(lib().radsort_device_status(stream), "device status")
+
+
+def radsort_trace_enable(on: bool):
+    _ok(lib().radsort_trace_enable(1 if on else 0), "radsort_trace_enable")
+
+
+def radsort_trace_read(cap: int = 1 << 16):
+    """[(phase_name, round, ms), ...] in launch order; clears the list."""
+    buf = (TraceRec * cap)()
+    cnt = ctypes.c_int(0)
+    _ok(lib().radsort_trace_read(buf, cap, ctypes.byref(cnt)), "radsort_trace_read")
+    return [(PHASES.get(buf[i].phase, "?"), int(buf[i].round), float(buf[i].ms))
+            for i in range(min(cnt.value, cap))]
+
+
+def radsort_launch_count() -> int:
+    v = ctypes.c_uint64(0)
+    _ok(lib().radsort_launch_count(ctypes.byref(v)), "radsort_launch_count")
+    return int(v.value)
 
 
 # ---------------------------------------------------------------- torch helpers
