@@ -98,61 +98,12 @@ static long env_long(const char *name, long dflt)
     return s && *s ? std::strtol(s, nullptr, 10) : dflt;
 }
 
-static size_t bookkeeping_per_block() { return 3 * 4; } // pi, pi', U
+static size_t layout(const Geom &g, void *base, Bufs *w);
 
-// Automatic plan.  The scratch array costs 2*sigma*p*b*E bytes, so the
-// plan trades chunk parallelism p against block size b.  It targets 2% of
-// the array's bytes when the array is large enough, and otherwise falls
-// back to small p.
-static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
-{
-    const uint32_t sigma = 1u << db;
-    const size_t E = kb + vb;
-    const double budget = 0.0195 * double(n) * double(E); // 2% with margin for alignment
-    const uint32_t pmax = static_cast<uint32_t>(num_sms());
-    // at least ~64K elements per chunk
-    uint32_t pcap = static_cast<uint32_t>(n / 65536);
-    if (pcap > pmax)
-        pcap = pmax;
-    if (pcap < 1)
-        pcap = 1;
-    uint32_t best_b = 512, best_p = 1;
-    const uint32_t cands[] = {256, 512, 1024, 2048};
-    for (uint32_t b : cands) {
-        if (db == 11 && n / b >= (1u << 20))
-            continue; // sequence numbers of a chunk's blocks need < 2^21
-        const double fixed = double(n / b) * bookkeeping_per_block();
-        const double per_p = 2.0 * sigma * b * double(E) + sigma * 24.0;
-        double pf = (budget - fixed) / per_p;
-        uint32_t p = pf < 1 ? 1 : (pf > pcap ? pcap : static_cast<uint32_t>(pf));
-        if (p > best_p || (p == best_p && b < best_b && best_p == 1)) {
-            best_p = p;
-            best_b = b;
-        }
-    }
-    if (best_p == 1 && n < (size_t(1) << 22))
-        best_b = 256;
-    pl->block_size = best_b;
-    pl->num_chunks = best_p;
-    long eb = env_long("RADSORT_B", 0), ep = env_long("RADSORT_P", 0);
-    if (eb > 0)
-        pl->block_size = static_cast<uint32_t>(eb);
-    if (ep > 0)
-        pl->num_chunks = static_cast<uint32_t>(ep);
-}
-
-static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radsort_plan *plan,
+// Geometry of a sort with block size b and p chunks (no planning).
+static radsort_status fill_geom(size_t n, int kb, bool hasv, int db, uint32_t b, uint32_t p,
                                 Geom *g)
 {
-    if ((kb != 4 && kb != 8) || (db != 8 && db != 11))
-        return RADSORT_EINVAL;
-    radsort_plan pl{};
-    auto_plan(n, kb, hasv ? 4 : 0, db, &pl);
-    if (plan && plan->block_size)
-        pl.block_size = plan->block_size;
-    if (plan && plan->num_chunks)
-        pl.num_chunks = plan->num_chunks;
-    const uint32_t b = pl.block_size, p = pl.num_chunks;
     if (!pow2(b) || b < 64 || b > 4096 || p < 1 || p > 65536)
         return RADSORT_EINVAL;
     g->n = n;
@@ -178,6 +129,78 @@ static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radso
     g->npi = static_cast<uint32_t>(npi);
     g->G = static_cast<uint32_t>(H);
     return RADSORT_OK;
+}
+
+// Automatic plan.  The scratch array costs 2*sigma*p*b*E bytes, so the plan
+// trades chunk parallelism p against block size b.  It keeps the whole
+// workspace within 2% of the array's bytes (with a floor for small arrays),
+// uses at most one chunk per SM and at least ~64K elements per chunk.
+static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
+{
+    const size_t E = kb + vb;
+    double budget = 0.02 * double(n) * double(E);
+    const double floor_bytes = double(env_long("RADSORT_MIN_WS_MB", 0)) * (1 << 20);
+    if (budget < floor_bytes)
+        budget = floor_bytes;
+    uint32_t pcap = static_cast<uint32_t>(n / 65536);
+    const uint32_t pmax = static_cast<uint32_t>(num_sms());
+    if (pcap > pmax)
+        pcap = pmax;
+    if (pcap < 1)
+        pcap = 1;
+    uint32_t best_b = 256, best_p = 0;
+    const uint32_t cands[] = {256, 512, 1024, 2048};
+    for (uint32_t b : cands) {
+        Geom g;
+        if (fill_geom(n, kb, vb != 0, db, b, 1, &g) != RADSORT_OK)
+            continue;
+        uint32_t lo = 1, hi = pcap; // largest p within the budget
+        if (double(layout(g, nullptr, nullptr)) > budget) {
+            hi = 0;
+        } else {
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) / 2;
+                if (fill_geom(n, kb, vb != 0, db, b, mid, &g) == RADSORT_OK &&
+                    double(layout(g, nullptr, nullptr)) <= budget)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+        }
+        if (hi > best_p) {
+            best_p = hi;
+            best_b = b;
+        }
+    }
+    if (best_p == 0) { // array too small for 2%: smallest sound plan
+        best_p = 1;
+        best_b = 256;
+        Geom g;
+        if (fill_geom(n, kb, vb != 0, db, best_b, 1, &g) != RADSORT_OK)
+            best_b = 2048;
+    }
+    pl->block_size = best_b;
+    pl->num_chunks = best_p;
+    long eb = env_long("RADSORT_B", 0), ep = env_long("RADSORT_P", 0);
+    if (eb > 0)
+        pl->block_size = static_cast<uint32_t>(eb);
+    if (ep > 0)
+        pl->num_chunks = static_cast<uint32_t>(ep);
+}
+
+static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radsort_plan *plan,
+                                Geom *g)
+{
+    if ((kb != 4 && kb != 8) || (db != 8 && db != 11))
+        return RADSORT_EINVAL;
+    radsort_plan pl{};
+    if (!plan || !plan->block_size || !plan->num_chunks)
+        auto_plan(n, kb, hasv ? 4 : 0, db, &pl);
+    if (plan && plan->block_size)
+        pl.block_size = plan->block_size;
+    if (plan && plan->num_chunks)
+        pl.num_chunks = plan->num_chunks;
+    return fill_geom(n, kb, hasv, db, pl.block_size, pl.num_chunks, g);
 }
 
 // Carves the workspace; with base == nullptr only computes the size.
