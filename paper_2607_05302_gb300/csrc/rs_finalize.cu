@@ -463,37 +463,91 @@ __device__ __forceinline__ void block_span(const FinArgs &a, uint32_t nP, uint32
     len = (l < nP && a.P[l].x == a.H + q) ? a.P[l].y : a.b;
 }
 
-// logical block holding element x
-__device__ uint32_t block_of(const FinArgs &a, uint32_t nP, unsigned long long x, uint32_t NL)
+// logical block holding element x (a non-empty one) and the number of
+// partial blocks before it.  Partial j (logical q_j) spans [off_j, end_j)
+// with off_j = q_j*b - D[j]; the blocks between partials are full.
+__device__ __forceinline__ void block_of(const FinArgs &a, uint32_t nP, unsigned long long x,
+                                         uint32_t &q, uint32_t &jp)
 {
-    uint32_t l = 0, r = NL; // last block with off <= x
-    while (l + 1 < r) {
+    uint32_t l = 0, r = nP; // J = first partial with end_J > x
+    while (l < r) {
         const uint32_t m = (l + r) >> 1;
-        unsigned long long off;
-        uint32_t len, jp;
-        block_span(a, nP, m, off, len, jp);
-        if (off <= x)
-            l = m;
+        const uint2 pm = a.P[m];
+        const unsigned long long end = (unsigned long long)(pm.x - a.H) * a.b - a.D[m] + pm.y;
+        if (end <= x)
+            l = m + 1;
         else
             r = m;
     }
-    for (;;) { // step over empty blocks that start at x
-        unsigned long long off;
-        uint32_t len, jp;
-        block_span(a, nP, l, off, len, jp);
-        if (x < off + len || l + 1 >= NL)
-            return l;
-        ++l;
+    jp = l;
+    if (l < nP) {
+        const uint2 pl = a.P[l];
+        const unsigned long long off = (unsigned long long)(pl.x - a.H) * a.b - a.D[l];
+        if (off <= x) {
+            q = pl.x - a.H;
+            return;
+        }
+    }
+    if (l == 0) {
+        q = static_cast<uint32_t>(x / a.b);
+        return;
+    }
+    const uint2 pp = a.P[l - 1];
+    const unsigned long long endp = (unsigned long long)(pp.x - a.H) * a.b - a.D[l - 1] + pp.y;
+    q = pp.x - a.H + 1 + static_cast<uint32_t>((x - endp) / a.b);
+}
+
+// number of partial blocks with logical index < H + q
+__device__ __forceinline__ uint32_t partials_before(const FinArgs &a, uint32_t nP, uint32_t q)
+{
+    uint32_t l = 0, r = nP;
+    while (l < r) {
+        const uint32_t m = (l + r) >> 1;
+        if (a.P[m].x < a.H + q)
+            l = m + 1;
+        else
+            r = m;
+    }
+    return l;
+}
+
+// per window: first source block, partials before it, the earliest window
+// that reads from this window's destinations, and whether it is in place
+__global__ void k_fz_winplan(FinArgs a, uint4 *plan)
+{
+    const uint32_t nP = a.state[ST_NP];
+    const unsigned long long n = a.n;
+    const uint32_t nwin = static_cast<uint32_t>((n + a.W - 1) / a.W);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwin; w += gridDim.x * blockDim.x) {
+        const unsigned long long x0 = (unsigned long long)w * a.W;
+        const uint32_t cnt = static_cast<uint32_t>(min((unsigned long long)a.W, n - x0));
+        uint32_t q0, jp0, qe, jpe;
+        block_of(a, nP, x0, q0, jp0);
+        block_of(a, nP, x0 + cnt - 1, qe, jpe);
+        // in place iff no partial block precedes the last block and it is in
+        // A: every source is then its own destination
+        const uint32_t inplace = (qe < a.nA && a.D[jpe] == 0) ? 1u : 0u;
+        // the destination of the element at virtual position x0 is the
+        // smallest destination among sources inside [x0, x0 + W)
+        const uint32_t qv = static_cast<uint32_t>(x0 / a.b);
+        uint32_t wlo = w; // destinations beyond A's blocks: nobody reads them
+        if (qv < a.nA) {
+            const uint32_t j = partials_before(a, nP, qv);
+            const unsigned long long offv = (unsigned long long)qv * a.b - a.D[j];
+            wlo = static_cast<uint32_t>(offv / a.W);
+        }
+        plan[w] = make_uint4(q0, jp0, wlo, inplace);
     }
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a)
+__global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *plan)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
     KT *wk = reinterpret_cast<KT *>(fsm);
     uint32_t *wv = reinterpret_cast<uint32_t *>(fsm + size_t(a.W) * sizeof(KT));
-    __shared__ uint32_t s_ticket, s_q0, s_wlo, s_inplace;
+    __shared__ uint32_t s_ticket;
+    __shared__ uint4 s_plan;
     const uint32_t nP = a.state[ST_NP];
     const uint32_t NL = a.state[ST_F] - a.H;
     const unsigned long long n = a.n;
@@ -501,41 +555,24 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a)
     const bool hv = a.Av != nullptr;
     KT *Ak = static_cast<KT *>(a.Ak);
     for (;;) {
-        if (threadIdx.x == 0)
-            s_ticket = atomicAdd(&a.ctr[C_WIN], 1u);
+        if (threadIdx.x == 0) {
+            const uint32_t t = atomicAdd(&a.ctr[C_WIN], 1u);
+            s_ticket = t;
+            if (t < nwin)
+                s_plan = plan[t];
+        }
         __syncthreads();
         const uint32_t w = s_ticket;
         if (w >= nwin)
             break;
+        const uint4 pl = s_plan;
         const unsigned long long x0 = (unsigned long long)w * a.W;
         const uint32_t cnt = static_cast<uint32_t>(min((unsigned long long)a.W, n - x0));
-        if (threadIdx.x == 0) {
-            s_q0 = block_of(a, nP, x0, NL);
-            // in place iff no partial block precedes the window's last block
-            // and that block lies in A: every source is its destination
-            const uint32_t qe = block_of(a, nP, x0 + cnt - 1, NL);
-            unsigned long long offe;
-            uint32_t lene, jpe;
-            block_span(a, nP, qe, offe, lene, jpe);
-            s_inplace = (qe < a.nA && a.D[jpe] == 0) ? 1u : 0u;
-            // earliest window whose sources lie in our destinations: the one
-            // holding the destination of the element at virtual position x0
-            const uint32_t qv = static_cast<uint32_t>(x0 / a.b);
-            if (qv < a.nA) {
-                unsigned long long offv;
-                uint32_t lenv, jpv;
-                block_span(a, nP, qv, offv, lenv, jpv);
-                s_wlo = static_cast<uint32_t>(offv / a.W);
-            } else {
-                s_wlo = w; // destinations beyond the blocks of A: nobody reads them
-            }
-        }
-        __syncthreads();
-        if (!s_inplace) {
+        if (!pl.w) {
             // read phase: the blocks covering destinations [x0, x0+cnt)
-            uint32_t q = s_q0, len, jp;
-            unsigned long long off;
-            block_span(a, nP, q, off, len, jp);
+            uint32_t q = pl.x, jp = pl.y;
+            unsigned long long off = (unsigned long long)q * a.b - a.D[jp];
+            uint32_t len = (jp < nP && a.P[jp].x == a.H + q) ? a.P[jp].y : a.b;
             uint32_t done = 0;
             while (done < cnt && q < NL) {
                 const uint32_t e0 = static_cast<uint32_t>(x0 + done - off);
@@ -564,9 +601,9 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a)
             __threadfence();
             st_release(&a.wflag[w], 1u);
         }
-        if (!s_inplace) {
+        if (!pl.w) {
             // wait for every earlier window that reads from our destinations
-            for (uint32_t v = s_wlo + threadIdx.x; v < w; v += blockDim.x)
+            for (uint32_t v = pl.z + threadIdx.x; v < w; v += blockDim.x)
                 wait_flag(&a.wflag[v]);
             __syncthreads();
             for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -580,7 +617,7 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a)
 }
 
 struct FinLayout {
-    size_t ctr, sflag, wflag, slotflag, rec, slotk, slotv, total;
+    size_t ctr, sflag, wflag, slotflag, rec, wplan, slotk, slotv, total;
     uint32_t K, W, nstr, nwin, nrec, nslots;
 };
 
@@ -611,6 +648,8 @@ FinLayout fin_layout(const Geom &g)
     off += al(size_t(L.nslots) * 4);
     L.rec = off; // everything before here is cleared per sort
     off += al(size_t(L.nrec) * 16);
+    L.wplan = off;
+    off += al(size_t(L.nwin) * 16);
     L.slotk = off;
     off += al(size_t(L.nslots) * g.b * g.kb);
     L.slotv = off;
@@ -696,9 +735,11 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_move<KT>, FIN_T, msm);
     k_fz_move<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, msm, st>>>(a);
     k_fz_move_deferred<KT><<<sms, FIN_T, msm, st>>>(a);
+    uint4 *wplan = reinterpret_cast<uint4 *>(base + L.wplan);
+    k_fz_winplan<<<(L.nwin + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, wplan);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_compact<KT>, FIN_T, csm);
-    k_fz_compact<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, csm, st>>>(a);
-    g_launches += 10 + 2 * rounds;
+    k_fz_compact<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, csm, st>>>(a, wplan);
+    g_launches += 11 + 2 * rounds;
     return cudaGetLastError();
 }
 
