@@ -116,18 +116,19 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES> struct R
     static constexpr int MAXM = TILE / 64;   // blocks per tile (b >= 64)
     static constexpr int PF = 2 * MAXM + 64; // free-list entries prefetched per tile
     static constexpr int R = TILE / NW;      // tile elements ranked per warp
+    static constexpr int ITEMS = R / 32;     // elements per consumer thread
     static_assert(R % 32 == 0, "warp range must be a multiple of 32");
     static constexpr size_t al(size_t x) { return (x + 127) & ~size_t(127); }
     static constexpr size_t o_stk = 0;
     static constexpr size_t o_stv = o_stk + al(size_t(STAGES) * TILE * sizeof(KT));
     static constexpr size_t o_sk = o_stv + (HASV ? al(size_t(STAGES) * TILE * 4) : 0);
     static constexpr size_t o_sv = o_sk + al(size_t(TILE) * sizeof(KT));
-    static constexpr size_t o_rank = o_sv + (HASV ? al(size_t(TILE) * 4) : 0);
-    static constexpr size_t o_hist = o_rank + al(size_t(TILE) * 2);
+    static constexpr size_t o_hist = o_sv + (HASV ? al(size_t(TILE) * 4) : 0);
     static constexpr size_t o_bk = o_hist + al(size_t(NW) * SIGMA * 2);
     static constexpr int NBK = 7; // tcnt, bstart, fill, cur, ccnt, nb, nbase
-    static constexpr size_t o_newblk = o_bk + al(size_t(NBK) * SIGMA * 4);
-    static constexpr size_t o_fl = o_newblk + al(size_t(SIGMA + MAXM + 1) * 4);
+    static constexpr size_t o_qb = o_bk + al(size_t(NBK) * SIGMA * 4);
+    static constexpr size_t o_list = o_qb + al(size_t(SIGMA) * 8);
+    static constexpr size_t o_fl = o_list + al(size_t(2 * SIGMA + MAXM + 1) * 4);
     static constexpr size_t o_meta = o_fl + al(size_t(PF) * 4);
     static constexpr size_t META = 16 + MAXM * 4; // nblk, m0, lens[MAXM]
     static constexpr size_t o_bar = o_meta + al(STAGES * META);
@@ -218,12 +219,15 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
     uint32_t *stv = reinterpret_cast<uint32_t *>(sm + C::o_stv);
     KT *sk = reinterpret_cast<KT *>(sm + C::o_sk);
     uint32_t *sv = reinterpret_cast<uint32_t *>(sm + C::o_sv);
-    uint16_t *rank16 = reinterpret_cast<uint16_t *>(sm + C::o_rank);
     uint16_t *hist = reinterpret_cast<uint16_t *>(sm + C::o_hist);
     uint32_t *bk = reinterpret_cast<uint32_t *>(sm + C::o_bk);
     uint32_t *tcnt = bk, *bstart = bk + SIGMA, *fill = bk + 2 * SIGMA, *cur = bk + 3 * SIGMA;
     uint32_t *ccnt = bk + 4 * SIGMA, *nb = bk + 5 * SIGMA, *nbase = bk + 6 * SIGMA;
-    uint32_t *newblk = reinterpret_cast<uint32_t *>(sm + C::o_newblk);
+    // per bucket: (chain offset of the tile's first element minus its tile
+    // start, index of the bucket's open block in `list`)
+    uint2 *qb = reinterpret_cast<uint2 *>(sm + C::o_qb);
+    // per bucket, contiguous: the open block, then the blocks opened in this tile
+    uint32_t *list = reinterpret_cast<uint32_t *>(sm + C::o_list);
     uint32_t *flbuf = reinterpret_cast<uint32_t *>(sm + C::o_fl);
     unsigned char *meta = sm + C::o_meta;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + C::o_bar);
@@ -389,26 +393,36 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         const KT *tk = stk + size_t(s) * TILE;
         const uint32_t *tv = stv + size_t(s) * TILE;
 
-        // ---- 1. stable rank within each warp's range
+        // ---- 1. load this thread's elements, rank them stably within the warp
         uint16_t *hw = hist + warp * SIGMA;
         for (int c = lane; c < SIGMA; c += 32)
             hw[c] = 0;
-        __syncwarp();
-        const unsigned lt = lanemask_lt();
-        for (int it = 0; it < C::R / 32; ++it) {
+        KT key[C::ITEMS];
+        uint32_t dig[C::ITEMS], rk[C::ITEMS];
+        unsigned peers[C::ITEMS];
+#pragma unroll
+        for (int it = 0; it < C::ITEMS; ++it) {
             const uint32_t e = warp * C::R + it * 32 + lane;
             const uint32_t slot = e >> a.lb, j = e & (b - 1);
             const bool valid = slot < nblk && j < lens[slot];
-            const uint32_t d = valid ? digit_of(tk[e], a.shift, mask) : SIGMA;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            key[it] = tk[e];
+            dig[it] = valid ? digit_of(key[it], a.shift, mask) : uint32_t(SIGMA);
+        }
+#pragma unroll
+        for (int it = 0; it < C::ITEMS; ++it)
+            peers[it] = __match_any_sync(0xffffffffu, dig[it]);
+        __syncwarp();
+        const unsigned lt = lanemask_lt();
+#pragma unroll
+        for (int it = 0; it < C::ITEMS; ++it) {
+            const uint32_t d = dig[it];
             uint32_t base = 0;
-            if (valid) {
+            if (d < SIGMA)
                 base = hw[d];
-                rank16[e] = static_cast<uint16_t>(base + __popc(peers & lt));
-            }
+            rk[it] = base + __popc(peers[it] & lt);
             __syncwarp();
-            if (valid && (__ffs(peers) - 1) == lane)
-                hw[d] = static_cast<uint16_t>(base + __popc(peers));
+            if (d < SIGMA && (__ffs(peers[it]) - 1) == lane)
+                hw[d] = static_cast<uint16_t>(base + __popc(peers[it]));
             __syncwarp();
         }
         named_bar(1, NT);
@@ -437,16 +451,17 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         if (tid == 0 && alloc + NB > SIGMA + m0 + nblk)
             set_status(ST_INTERNAL); // Lemma 1 would be violated
         for (int c = tid; c < SIGMA; c += NT) {
-            const uint32_t k0 = nbase[c], cnt = nb[c];
+            const uint32_t k0 = nbase[c], cnt = nb[c], l0 = k0 + c;
+            qb[c] = make_uint2(fill[c] - bstart[c], l0);
+            list[l0] = cur[c];
             for (uint32_t i = 0; i < cnt; ++i) {
                 const uint32_t k = alloc + k0 + i; // free-list index
                 if (k >= fl_len) { // cannot happen (Lemma 1); never write past the list
-                    newblk[k0 + i] = NO_BLOCK;
+                    list[l0 + 1 + i] = NO_BLOCK;
                     continue;
                 }
                 const uint32_t r = k - fl0;
-                const uint32_t phys = r < C::PF ? flbuf[r] : a.pi[fl_index(k)];
-                newblk[k0 + i] = phys;
+                list[l0 + 1 + i] = r < C::PF ? flbuf[r] : a.pi[fl_index(k)];
                 a.UC[fl_index(k)] = (uint32_t(c) << SB) | (ccnt[c] + i);
             }
         }
@@ -457,16 +472,14 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         }
 
         // ---- 4a. reorder the tile by digit in shared memory
-        for (int it = 0; it < C::R / 32; ++it) {
-            const uint32_t e = warp * C::R + it * 32 + lane;
-            const uint32_t slot = e >> a.lb, j = e & (b - 1);
-            if (slot < nblk && j < lens[slot]) {
-                const KT key = tk[e];
-                const uint32_t d = digit_of(key, a.shift, mask);
-                const uint32_t pos = bstart[d] + hist[warp * SIGMA + d] + rank16[e];
-                sk[pos] = key;
+#pragma unroll
+        for (int it = 0; it < C::ITEMS; ++it) {
+            const uint32_t d = dig[it];
+            if (d < SIGMA) {
+                const uint32_t pos = bstart[d] + hist[warp * SIGMA + d] + rk[it];
+                sk[pos] = key[it];
                 if (HASV)
-                    sv[pos] = tv[e];
+                    sv[pos] = tv[warp * C::R + it * 32 + lane];
             }
         }
         named_bar(1, NT);
@@ -474,18 +487,22 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
             mbar_arrive(&empty[s]); // stage consumed: the producer may refill it
 
         // ---- 4b. store every bucket run into its block chain
-        for (uint32_t i = tid; i < nvalid; i += NT) {
-            const KT key = sk[i];
-            const uint32_t d = digit_of(key, a.shift, mask);
-            const uint32_t qpos = fill[d] + (i - bstart[d]);
-            const uint32_t o = qpos >> a.lb, off = qpos & (b - 1);
-            const uint32_t blk = o ? newblk[nbase[d] + o - 1] : cur[d];
-            if (blk == NO_BLOCK)
-                continue;
-            const size_t eoff = (blk < a.nT ? size_t(blk) : size_t(blk - a.nT)) * b + off;
-            (blk < a.nT ? a.Tk : a.Ak)[eoff] = key;
-            if (HASV)
-                (blk < a.nT ? a.Tv : a.Av)[eoff] = sv[i];
+        constexpr int SI = (TILE + NT - 1) / NT;
+#pragma unroll
+        for (int k = 0; k < SI; ++k) {
+            const uint32_t i = tid + k * NT;
+            if (i < nvalid) {
+                const KT kk = sk[i];
+                const uint2 qd = qb[digit_of(kk, a.shift, mask)];
+                const uint32_t qpos = i + qd.x;
+                const uint32_t blk = list[qd.y + (qpos >> a.lb)];
+                if (blk != NO_BLOCK) {
+                    const size_t eoff = (blk < a.nT ? size_t(blk) : size_t(blk - a.nT)) * b + (qpos & (b - 1));
+                    (blk < a.nT ? a.Tk : a.Ak)[eoff] = kk;
+                    if (HASV)
+                        (blk < a.nT ? a.Tv : a.Av)[eoff] = sv[i];
+                }
+            }
         }
         named_bar(1, NT);
 
@@ -494,7 +511,7 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
             const uint32_t cnt = nb[c];
             fill[c] = (fill[c] + tcnt[c]) & (b - 1);
             if (cnt) {
-                cur[c] = newblk[nbase[c] + cnt - 1];
+                cur[c] = list[nbase[c] + c + cnt];
                 ccnt[c] += cnt;
             }
         }
