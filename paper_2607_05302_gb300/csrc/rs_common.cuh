@@ -130,6 +130,21 @@ __device__ __forceinline__ void named_bar(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Mask of the lanes whose digit equals this lane's, among lanes with
+// `valid` set: one ballot per digit bit (warp-level multisplit).  All 32
+// lanes must call it.
+template <int DB> __device__ __forceinline__ unsigned peer_mask(uint32_t d, bool valid)
+{
+    unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int bit = 0; bit < DB; ++bit) {
+        const bool on = (d >> bit) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, on);
+        m &= on ? bal : ~bal;
+    }
+    return m;
+}
+
 // ---------------------------------------------------------------- keys
 template <typename KT> __device__ __forceinline__ uint32_t digit_of(KT k, uint32_t shift,
                                                                      uint32_t mask)

@@ -4,7 +4,7 @@
 // One upfront pass histograms every digit position in a single read of the
 // keys (the paper's "generic" variant, Sec. 5).  Each round then makes one
 // pass A -> A'.  A tile takes a ticket (dispatch order), ranks its digits
-// stably (__match_any_sync + per-warp histograms) and publishes its per-digit
+// stably (ballot-per-bit peer masks + per-warp histograms) and publishes its per-digit
 // counts.  It gets its exclusive per-digit prefix by a decoupled look-back
 // over earlier tiles, with bounded spins, and stores each digit run
 // contiguously from a digit-sorted copy in shared memory.  The look-back
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const uint32_t e = warp * C::R + it * 32 + lane;
             const bool valid = e < cnt;
             const uint32_t d = valid ? digit_of(tk[e], shift, mask) : SIGMA;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const unsigned peers = peer_mask<DB>(d, valid);
             uint32_t base = 0;
             if (valid) {
                 base = hw[d];

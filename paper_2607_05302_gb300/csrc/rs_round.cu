@@ -11,8 +11,10 @@
 // Per CTA: a producer warp streams the chunk's input blocks into a ring of
 // shared-memory stages with 1-D bulk copies (TMA) completing on mbarriers.
 // The consumer warps then, for each tile of M = TILE/b blocks:
-//   1. rank the tile's digits stably: __match_any_sync gives the rank among a
-//      warp's equal digits; per-warp histograms give each warp's offset;
+//   1. rank the tile's digits stably: a per-warp shared-memory table of lane
+//      masks (atomicOr by digit) gives each lane the set of lanes with its
+//      digit, hence its rank among a warp's equal digits; per-warp
+//      histograms give each warp's offset;
 //   2. scan the tile histogram for bucket starts inside the tile;
 //   3. count the blocks each bucket fills and take that many new blocks
 //      from the free list (newBucketBlock, eagerly, as in Alg. 5), recording
@@ -118,22 +120,42 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES> struct R
     static constexpr int R = TILE / NW;      // tile elements ranked per warp
     static constexpr int ITEMS = R / 32;     // elements per consumer thread
     static_assert(R % 32 == 0, "warp range must be a multiple of 32");
+    static_assert(THREADS <= 1024, "one CTA holds at most 1024 threads");
+    // column scan over the warps' counts: TPB threads per bucket, in
+    // different warps (consecutive lanes take consecutive buckets)
+    static constexpr int TPB = NT >= 2 * SIGMA ? 2 : 1;
+    static_assert(NW % TPB == 0, "rows split evenly");
+    // sigma <= 256: a per-warp 64-bit table per digit holds (running count
+    // << 32 | lane mask); shared-memory atomicOr builds the mask, far cheaper
+    // here than __match_any_sync or a ballot per digit bit.  sigma = 2048:
+    // ballot-per-bit masks and a 16-bit count table.
+    static constexpr bool PTAB = DB <= 8;
+    // 32-bit key + 32-bit value: the in-place reorder writes (key, value)
+    // pairs as one 8-byte word
+    static constexpr bool PAIR = HASV && sizeof(KT) == 4;
+    static constexpr int HROW = SIGMA + 2; // padded u16 histogram row
     static constexpr size_t al(size_t x) { return (x + 127) & ~size_t(127); }
-    static constexpr size_t o_stk = 0;
-    static constexpr size_t o_stv = o_stk + al(size_t(STAGES) * TILE * sizeof(KT));
-    static constexpr size_t o_sk = o_stv + (HASV ? al(size_t(STAGES) * TILE * 4) : 0);
-    static constexpr size_t o_sv = o_sk + al(size_t(TILE) * sizeof(KT));
-    static constexpr size_t o_hist = o_sv + (HASV ? al(size_t(TILE) * 4) : 0);
-    static constexpr size_t o_bk = o_hist + al(size_t(NW) * SIGMA * 2);
-    static constexpr int NBK = 7; // tcnt, bstart, fill, cur, ccnt, nb, nbase
-    static constexpr size_t o_qb = o_bk + al(size_t(NBK) * SIGMA * 4);
-    static constexpr size_t o_list = o_qb + al(size_t(SIGMA) * 8);
-    static constexpr size_t o_fl = o_list + al(size_t(2 * SIGMA + MAXM + 1) * 4);
+    static constexpr size_t KBYTES = size_t(TILE) * sizeof(KT);
+    static constexpr size_t STAGE = al(KBYTES + (HASV ? size_t(TILE) * 4 : 0));
+    static constexpr size_t o_stage = 0;
+    static constexpr size_t o_hist = o_stage + STAGES * STAGE;
+    static constexpr size_t o_tab = o_hist + al(size_t(NW) * HROW * 2);
+    static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * SIGMA * 8) : 0);
+    static constexpr int NBK = 8; // tcnt, bstart, fill, cur, ccnt, nb, nbase, ncur
+    static constexpr size_t o_psum = o_bk + al(size_t(NBK) * SIGMA * 4);
+    static constexpr size_t o_qb = o_psum + al(size_t(TPB) * SIGMA * 4);
+    static constexpr int LIST = 2 * SIGMA + MAXM + 1;
+    // sigma <= 256: the block lists hold key/value pointers; sigma = 2048
+    // (shared memory is tight): block indices
+    static constexpr bool LPTR = DB <= 8;
+    static constexpr size_t o_lk = o_qb + al(size_t(SIGMA) * 8);
+    static constexpr size_t o_lv = o_lk + al(size_t(LIST) * (LPTR ? 8 : 4));
+    static constexpr size_t o_fl = o_lv + (HASV && LPTR ? al(size_t(LIST) * 8) : 0);
     static constexpr size_t o_meta = o_fl + al(size_t(PF) * 4);
     static constexpr size_t META = 16 + MAXM * 4; // nblk, m0, lens[MAXM]
     static constexpr size_t o_bar = o_meta + al(STAGES * META);
     static constexpr size_t o_misc = o_bar + al(2 * STAGES * 8);
-    static constexpr size_t SMEM = o_misc + 256;
+    static constexpr size_t SMEM = o_misc + 512;
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 
@@ -215,25 +237,27 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
     constexpr int SIGMA = C::SIGMA, NT = C::NT;
     constexpr uint32_t SB = 32 - DB; // UC: bucket in the top DB bits, sequence below
     extern __shared__ __align__(128) unsigned char sm[];
-    KT *stk = reinterpret_cast<KT *>(sm + C::o_stk);
-    uint32_t *stv = reinterpret_cast<uint32_t *>(sm + C::o_stv);
-    KT *sk = reinterpret_cast<KT *>(sm + C::o_sk);
-    uint32_t *sv = reinterpret_cast<uint32_t *>(sm + C::o_sv);
     uint16_t *hist = reinterpret_cast<uint16_t *>(sm + C::o_hist);
+    unsigned long long *tab = reinterpret_cast<unsigned long long *>(sm + C::o_tab);
     uint32_t *bk = reinterpret_cast<uint32_t *>(sm + C::o_bk);
     uint32_t *tcnt = bk, *bstart = bk + SIGMA, *fill = bk + 2 * SIGMA, *cur = bk + 3 * SIGMA;
     uint32_t *ccnt = bk + 4 * SIGMA, *nb = bk + 5 * SIGMA, *nbase = bk + 6 * SIGMA;
-    // per bucket: (chain offset of the tile's first element minus its tile
-    // start, index of the bucket's open block in `list`)
+    uint32_t *ncur = bk + 7 * SIGMA;
+    uint32_t *psum = reinterpret_cast<uint32_t *>(sm + C::o_psum);
+    // per bucket: (chain offset of the tile's first element minus its start
+    // in the reordered tile, index of the bucket's open block in the lists)
     uint2 *qb = reinterpret_cast<uint2 *>(sm + C::o_qb);
-    // per bucket, contiguous: the open block, then the blocks opened in this tile
-    uint32_t *list = reinterpret_cast<uint32_t *>(sm + C::o_list);
+    // per bucket, contiguous: the open block, then the blocks opened in this
+    // tile, as key and value pointers
+    KT **listk = reinterpret_cast<KT **>(sm + C::o_lk);
+    uint32_t **listv = reinterpret_cast<uint32_t **>(sm + C::o_lv);
+    uint32_t *listb = reinterpret_cast<uint32_t *>(sm + C::o_lk); // !LPTR: block indices
     uint32_t *flbuf = reinterpret_cast<uint32_t *>(sm + C::o_fl);
     unsigned char *meta = sm + C::o_meta;
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + C::o_bar);
     uint64_t *empty = full + STAGES;
     uint32_t *misc = reinterpret_cast<uint32_t *>(sm + C::o_misc);
-    // misc: [0] consumed tiles, [1] abort, [8..] scan scratch
+    // misc: [0] consumed tiles, [8..] scan scratch
 
     const uint32_t q = blockIdx.x;
     const uint32_t b = 1u << a.lb, M = static_cast<uint32_t>(TILE) >> a.lb;
@@ -248,13 +272,18 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
             mbar_init(&empty[s], 1);
         }
         misc[0] = 0;
-        misc[1] = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
     // old-pi index of free-list entry k
     auto fl_index = [&](uint32_t k) -> uint32_t { return k < SIGMA ? q * SIGMA + k : lo + (k - SIGMA); };
+    auto kaddr = [&](uint32_t blk) -> KT * {
+        return blk < a.nT ? a.Tk + size_t(blk) * b : a.Ak + size_t(blk - a.nT) * b;
+    };
+    auto vaddr = [&](uint32_t blk) -> uint32_t * {
+        return blk < a.nT ? a.Tv + size_t(blk) * b : a.Av + size_t(blk - a.nT) * b;
+    };
 
     if (warp == NW) {
         // ================================================================ producer
@@ -273,14 +302,11 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
             ip = l;
         }
         uint32_t m = 0, tile = 0;
-        bool ok = true;
         for (;; ++tile) {
             const int s = tile % STAGES;
             const uint32_t par = ((tile / STAGES) & 1u) ^ 1u;
-            if (!mbar_wait(&empty[s], par)) {
-                ok = false;
+            if (!mbar_wait(&empty[s], par))
                 break;
-            }
             uint32_t *mt = reinterpret_cast<uint32_t *>(meta + s * C::META);
             if (m >= nblocks) {
                 if (lane == 0) {
@@ -290,6 +316,9 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
                 ++tile;
                 break;
             }
+            unsigned char *st = sm + C::o_stage + size_t(s) * C::STAGE;
+            KT *stk = reinterpret_cast<KT *>(st);
+            uint32_t *stv = reinterpret_cast<uint32_t *>(st + C::KBYTES);
             const uint32_t Mt = min(M, nblocks - m);
             uint32_t *lens = mt + 4;
             for (uint32_t base = 0; base < Mt; base += 32) {
@@ -326,15 +355,9 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
                                  : "memory");
                 __syncwarp();
                 if (j < Mt && len) {
-                    const size_t off = phys < a.nT ? size_t(phys) * b : size_t(phys - a.nT) * b;
-                    const KT *srck = (phys < a.nT ? a.Tk : a.Ak) + off;
-                    bulk_g2s(stk + size_t(s) * TILE + size_t(j) * b, srck,
-                             (len * sizeof(KT) + 15u) & ~15u, &full[s]);
-                    if (HASV) {
-                        const uint32_t *srcv = (phys < a.nT ? a.Tv : a.Av) + off;
-                        bulk_g2s(stv + size_t(s) * TILE + size_t(j) * b, srcv, (len * 4u + 15u) & ~15u,
-                                 &full[s]);
-                    }
+                    bulk_g2s(stk + size_t(j) * b, kaddr(phys), (len * sizeof(KT) + 15u) & ~15u, &full[s]);
+                    if (HASV)
+                        bulk_g2s(stv + size_t(j) * b, vaddr(phys), (len * 4u + 15u) & ~15u, &full[s]);
                 }
             }
             if (lane == 0) {
@@ -346,9 +369,8 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
                 mbar_arrive(&full[s]);
             m += Mt;
         }
-        // drain: every issued copy must land before this CTA exits
-        // (only the last STAGES issued tiles can still be in flight; an older
-        // stage phase has been consumed and overwritten)
+        // drain: every issued copy must land before this CTA exits (only the
+        // last STAGES issued tiles can still be in flight)
         if (lane == 0) {
             const uint32_t done = *(volatile uint32_t *)&misc[0];
             uint32_t t0 = tile > STAGES ? tile - STAGES : 0;
@@ -357,7 +379,6 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
             for (uint32_t t = t0; t < tile; ++t)
                 mbar_wait(&full[t % STAGES], (t / STAGES) & 1u);
         }
-        (void)ok;
         return;
     }
 
@@ -390,57 +411,114 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         }
         const uint32_t m0 = mt[1];
         const uint32_t *lens = mt + 4;
-        const KT *tk = stk + size_t(s) * TILE;
-        const uint32_t *tv = stv + size_t(s) * TILE;
+        unsigned char *st = sm + C::o_stage + size_t(s) * C::STAGE;
+        KT *tk = reinterpret_cast<KT *>(st);
+        uint32_t *tv = reinterpret_cast<uint32_t *>(st + C::KBYTES);
+        uint2 *tp = reinterpret_cast<uint2 *>(st); // (key, value) pairs after the reorder
 
-        // ---- 1. load this thread's elements, rank them stably within the warp
-        uint16_t *hw = hist + warp * SIGMA;
-        for (int c = lane; c < SIGMA; c += 32)
-            hw[c] = 0;
+        // ---- 1. this thread's elements into registers; stable rank within the warp
         KT key[C::ITEMS];
-        uint32_t dig[C::ITEMS], rk[C::ITEMS];
-        unsigned peers[C::ITEMS];
+        uint32_t val[C::ITEMS], dig[C::ITEMS], rk[C::ITEMS];
 #pragma unroll
         for (int it = 0; it < C::ITEMS; ++it) {
             const uint32_t e = warp * C::R + it * 32 + lane;
             const uint32_t slot = e >> a.lb, j = e & (b - 1);
             const bool valid = slot < nblk && j < lens[slot];
             key[it] = tk[e];
+            if (HASV)
+                val[it] = tv[e];
             dig[it] = valid ? digit_of(key[it], a.shift, mask) : uint32_t(SIGMA);
         }
-#pragma unroll
-        for (int it = 0; it < C::ITEMS; ++it)
-            peers[it] = __match_any_sync(0xffffffffu, dig[it]);
-        __syncwarp();
         const unsigned lt = lanemask_lt();
+        if constexpr (C::PTAB) {
+            // row by row: lanes with the same digit OR their bit into the
+            // digit's table word and read back (count << 32 | lanes); the
+            // lowest of those lanes stores the advanced count with an empty
+            // lane mask.  Each warp zeroes its row first.
+            unsigned long long *tw = tab + warp * SIGMA;
+            for (int c = lane; c < SIGMA; c += 32)
+                tw[c] = 0ull;
+            __syncwarp();
 #pragma unroll
-        for (int it = 0; it < C::ITEMS; ++it) {
-            const uint32_t d = dig[it];
-            uint32_t base = 0;
-            if (d < SIGMA)
-                base = hw[d];
-            rk[it] = base + __popc(peers[it] & lt);
+            for (int it = 0; it < C::ITEMS; ++it) {
+                const uint32_t d = dig[it];
+                const bool v = d < SIGMA;
+                if (v)
+                    atomicOr(&tw[d], 1ull << lane);
+                __syncwarp();
+                const unsigned long long ent = v ? tw[d] : 0ull;
+                const unsigned pm = static_cast<unsigned>(ent);
+                const uint32_t base = static_cast<uint32_t>(ent >> 32);
+                rk[it] = base + __popc(pm & lt);
+                __syncwarp();
+                if (v && (__ffs(pm) - 1) == lane)
+                    tw[d] = static_cast<unsigned long long>(base + __popc(pm)) << 32;
+                __syncwarp();
+            }
+        } else {
+            uint16_t *hw = hist + warp * C::HROW;
+            for (int c = lane; c < SIGMA; c += 32)
+                hw[c] = 0;
+            unsigned peers[C::ITEMS];
+#pragma unroll
+            for (int it = 0; it < C::ITEMS; ++it)
+                peers[it] = peer_mask<DB>(dig[it], dig[it] < SIGMA);
             __syncwarp();
-            if (d < SIGMA && (__ffs(peers[it]) - 1) == lane)
-                hw[d] = static_cast<uint16_t>(base + __popc(peers[it]));
-            __syncwarp();
+#pragma unroll
+            for (int it = 0; it < C::ITEMS; ++it) {
+                const uint32_t d = dig[it];
+                uint32_t base = 0;
+                if (d < SIGMA)
+                    base = hw[d];
+                rk[it] = base + __popc(peers[it] & lt);
+                __syncwarp();
+                if (d < SIGMA && (__ffs(peers[it]) - 1) == lane)
+                    hw[d] = static_cast<uint16_t>(base + __popc(peers[it]));
+                __syncwarp();
+            }
         }
         named_bar(1, NT);
 
-        // ---- 2. per-bucket warp offsets and tile counts
-        for (int c = tid; c < SIGMA; c += NT) {
-            uint32_t run = 0;
-#pragma unroll 4
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t h = hist[w * SIGMA + c];
-                hist[w * SIGMA + c] = static_cast<uint16_t>(run);
-                run += h;
+        // ---- 2. per-bucket warp offsets (exclusive over warps) and tile counts
+        {
+            constexpr int RPT = NW / C::TPB;
+            auto count = [&](int w, int c) -> uint32_t {
+                if constexpr (C::PTAB)
+                    return static_cast<uint32_t>(tab[w * SIGMA + c] >> 32);
+                else
+                    return hist[w * C::HROW + c];
+            };
+            for (int t = tid; t < SIGMA * C::TPB; t += NT) {
+                const int c = t % SIGMA, part = t / SIGMA;
+                uint32_t sum = 0;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r)
+                    sum += count(part * RPT + r, c);
+                psum[part * SIGMA + c] = sum;
             }
-            tcnt[c] = run;
-            bstart[c] = run;
-            const uint32_t fnew = fill[c] + run;
-            nb[c] = fnew >> a.lb; // blocks filled -> new blocks (eager, Alg. 5)
-            nbase[c] = fnew >> a.lb;
+            named_bar(1, NT);
+            for (int t = tid; t < SIGMA * C::TPB; t += NT) {
+                const int c = t % SIGMA, part = t / SIGMA;
+                uint32_t run = 0;
+#pragma unroll
+                for (int pp = 0; pp < C::TPB; ++pp)
+                    if (pp < part)
+                        run += psum[pp * SIGMA + c];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const int w = part * RPT + r;
+                    const uint32_t h = count(w, c);
+                    hist[w * C::HROW + c] = static_cast<uint16_t>(run);
+                    run += h;
+                }
+                if (part == C::TPB - 1) {
+                    tcnt[c] = run;
+                    bstart[c] = run;
+                    const uint32_t fnew = fill[c] + run;
+                    nb[c] = fnew >> a.lb; // blocks filled -> new blocks (eager, Alg. 5)
+                    nbase[c] = fnew >> a.lb;
+                }
+            }
         }
         named_bar(1, NT);
         uint32_t nvalid, NB;
@@ -453,17 +531,31 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         for (int c = tid; c < SIGMA; c += NT) {
             const uint32_t k0 = nbase[c], cnt = nb[c], l0 = k0 + c;
             qb[c] = make_uint2(fill[c] - bstart[c], l0);
-            list[l0] = cur[c];
+            if constexpr (C::LPTR) {
+                listk[l0] = kaddr(cur[c]);
+                if (HASV)
+                    listv[l0] = vaddr(cur[c]);
+            } else {
+                listb[l0] = cur[c];
+            }
+            uint32_t last = cur[c];
             for (uint32_t i = 0; i < cnt; ++i) {
                 const uint32_t k = alloc + k0 + i; // free-list index
-                if (k >= fl_len) { // cannot happen (Lemma 1); never write past the list
-                    list[l0 + 1 + i] = NO_BLOCK;
-                    continue;
+                uint32_t blk = NO_BLOCK;
+                if (k < fl_len) { // always (Lemma 1); never take past the list
+                    const uint32_t r = k - fl0;
+                    blk = last = r < C::PF ? flbuf[r] : a.pi[fl_index(k)];
+                    a.UC[fl_index(k)] = (uint32_t(c) << SB) | (ccnt[c] + i);
                 }
-                const uint32_t r = k - fl0;
-                list[l0 + 1 + i] = r < C::PF ? flbuf[r] : a.pi[fl_index(k)];
-                a.UC[fl_index(k)] = (uint32_t(c) << SB) | (ccnt[c] + i);
+                if constexpr (C::LPTR) {
+                    listk[l0 + 1 + i] = blk == NO_BLOCK ? nullptr : kaddr(blk);
+                    if (HASV)
+                        listv[l0 + 1 + i] = blk == NO_BLOCK ? nullptr : vaddr(blk);
+                } else {
+                    listb[l0 + 1 + i] = blk;
+                }
             }
+            ncur[c] = last;
         }
         {   // prefetch the free-list entries the next tile may take
             const uint32_t k = alloc + NB + tid;
@@ -471,20 +563,23 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
                 pfv = a.pi[fl_index(k)];
         }
 
-        // ---- 4a. reorder the tile by digit in shared memory
+        // ---- 4a. reorder the tile by digit, in place in its stage buffer
+        // (every element is in registers since the barriers above)
 #pragma unroll
         for (int it = 0; it < C::ITEMS; ++it) {
             const uint32_t d = dig[it];
             if (d < SIGMA) {
-                const uint32_t pos = bstart[d] + hist[warp * SIGMA + d] + rk[it];
-                sk[pos] = key[it];
-                if (HASV)
-                    sv[pos] = tv[warp * C::R + it * 32 + lane];
+                const uint32_t pos = bstart[d] + hist[warp * C::HROW + d] + rk[it];
+                if constexpr (C::PAIR) {
+                    tp[pos] = make_uint2(static_cast<uint32_t>(key[it]), val[it]);
+                } else {
+                    tk[pos] = key[it];
+                    if (HASV)
+                        tv[pos] = val[it];
+                }
             }
         }
         named_bar(1, NT);
-        if (tid == 0)
-            mbar_arrive(&empty[s]); // stage consumed: the producer may refill it
 
         // ---- 4b. store every bucket run into its block chain
         constexpr int SI = (TILE + NT - 1) / NT;
@@ -492,28 +587,47 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         for (int k = 0; k < SI; ++k) {
             const uint32_t i = tid + k * NT;
             if (i < nvalid) {
-                const KT kk = sk[i];
+                KT kk;
+                uint32_t vv = 0;
+                if constexpr (C::PAIR) {
+                    const uint2 pr = tp[i];
+                    kk = pr.x;
+                    vv = pr.y;
+                } else {
+                    kk = tk[i];
+                    if (HASV)
+                        vv = tv[i];
+                }
                 const uint2 qd = qb[digit_of(kk, a.shift, mask)];
                 const uint32_t qpos = i + qd.x;
-                const uint32_t blk = list[qd.y + (qpos >> a.lb)];
-                if (blk != NO_BLOCK) {
-                    const size_t eoff = (blk < a.nT ? size_t(blk) : size_t(blk - a.nT)) * b + (qpos & (b - 1));
-                    (blk < a.nT ? a.Tk : a.Ak)[eoff] = kk;
-                    if (HASV)
-                        (blk < a.nT ? a.Tv : a.Av)[eoff] = sv[i];
+                const uint32_t l = qd.y + (qpos >> a.lb), off = qpos & (b - 1);
+                if constexpr (C::LPTR) {
+                    KT *pk = listk[l];
+                    if (pk) {
+                        pk[off] = kk;
+                        if (HASV)
+                            listv[l][off] = vv;
+                    }
+                } else {
+                    const uint32_t blk = listb[l];
+                    if (blk != NO_BLOCK) {
+                        kaddr(blk)[off] = kk;
+                        if (HASV)
+                            vaddr(blk)[off] = vv;
+                    }
                 }
             }
         }
         named_bar(1, NT);
+        if (tid == 0)
+            mbar_arrive(&empty[s]); // stage consumed: the producer may refill it
 
         // ---- 5. bucket state after the tile
         for (int c = tid; c < SIGMA; c += NT) {
             const uint32_t cnt = nb[c];
             fill[c] = (fill[c] + tcnt[c]) & (b - 1);
-            if (cnt) {
-                cur[c] = list[nbase[c] + c + cnt];
-                ccnt[c] += cnt;
-            }
+            cur[c] = ncur[c];
+            ccnt[c] += cnt;
         }
         alloc += NB;
         fl0 = alloc;
@@ -570,16 +684,17 @@ cudaError_t launch_round(const Geom &g, const Bufs &w, const uint32_t *pi, const
                          uint32_t *UC, int round, cudaStream_t st)
 {
     using u64 = unsigned long long;
+    //                       key  vals  d   TILE  NW  STAGES
     if (g.kb == 4) {
         if (g.db == 8)
-            return g.hasv ? round_impl<uint32_t, true, 8, 4096, 16, 3>(g, w, pi, lo, UC, round, st)
-                          : round_impl<uint32_t, false, 8, 4096, 16, 3>(g, w, pi, lo, UC, round, st);
+            return g.hasv ? round_impl<uint32_t, true, 8, 8192, 16, 2>(g, w, pi, lo, UC, round, st)
+                          : round_impl<uint32_t, false, 8, 8192, 16, 3>(g, w, pi, lo, UC, round, st);
         return g.hasv ? round_impl<uint32_t, true, 11, 4096, 8, 2>(g, w, pi, lo, UC, round, st)
-                      : round_impl<uint32_t, false, 11, 4096, 8, 2>(g, w, pi, lo, UC, round, st);
+                      : round_impl<uint32_t, false, 11, 4096, 8, 3>(g, w, pi, lo, UC, round, st);
     }
     if (g.db == 8)
-        return g.hasv ? round_impl<u64, true, 8, 4096, 16, 2>(g, w, pi, lo, UC, round, st)
-                      : round_impl<u64, false, 8, 4096, 16, 3>(g, w, pi, lo, UC, round, st);
+        return g.hasv ? round_impl<u64, true, 8, 4096, 16, 3>(g, w, pi, lo, UC, round, st)
+                      : round_impl<u64, false, 8, 8192, 16, 2>(g, w, pi, lo, UC, round, st);
     return g.hasv ? round_impl<u64, true, 11, 2048, 8, 3>(g, w, pi, lo, UC, round, st)
                   : round_impl<u64, false, 11, 4096, 8, 2>(g, w, pi, lo, UC, round, st);
 }
