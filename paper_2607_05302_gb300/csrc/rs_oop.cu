@@ -4,7 +4,8 @@
 // One upfront pass histograms every digit position in a single read of the
 // keys (the paper's "generic" variant, Sec. 5).  Each round then makes one
 // pass A -> A'.  A tile takes a ticket (dispatch order), ranks its digits
-// stably (ballot-per-bit peer masks + per-warp histograms) and publishes its per-digit
+// stably (lane masks by digit from a shared-memory atomicOr table, or a
+// ballot per digit bit for 11-bit digits, plus per-warp histograms) and publishes its per-digit
 // counts.  It gets its exclusive per-digit prefix by a decoupled look-back
 // over earlier tiles, with bounded spins, and stores each digit run
 // contiguously from a digit-sorted copy in shared memory.  The look-back
@@ -73,7 +74,9 @@ template <typename KT, bool HASV, int DB, int TILE, int NW> struct OopCfg {
     static constexpr size_t o_rank = o_sv + (HASV ? al(size_t(TILE) * 4) : 0);
     static constexpr size_t o_hist = o_rank + al(size_t(TILE) * 2);
     static constexpr size_t o_bk = o_hist + al(size_t(NW) * SIGMA * 2);
-    static constexpr size_t o_misc = o_bk + al(size_t(SIGMA) * 16); // tcnt, bstart, gbase(u64)
+    static constexpr bool PTAB = DB <= 8; // lane masks by digit via shared atomicOr
+    static constexpr size_t o_ptab = o_bk + al(size_t(SIGMA) * 16); // after tcnt, bstart, gbase(u64)
+    static constexpr size_t o_misc = o_ptab + (PTAB ? al(size_t(NW) * SIGMA * 4) : 0);
     static constexpr size_t SMEM = o_misc + 256;
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -96,6 +99,10 @@ __global__ void __launch_bounds__(NW * 32, 1)
     uint32_t *bstart = tcnt + SIGMA;
     unsigned long long *gbase = reinterpret_cast<unsigned long long *>(bstart + SIGMA);
     uint32_t *misc = reinterpret_cast<uint32_t *>(sm + C::o_misc);
+    unsigned *ptab = reinterpret_cast<unsigned *>(sm + C::o_ptab);
+    if constexpr (C::PTAB)
+        for (int i = threadIdx.x; i < NW * SIGMA; i += blockDim.x)
+            ptab[i] = 0u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t mask = SIGMA - 1;
     const size_t ntiles = (n + TILE - 1) / TILE;
@@ -123,7 +130,19 @@ __global__ void __launch_bounds__(NW * 32, 1)
             const uint32_t e = warp * C::R + it * 32 + lane;
             const bool valid = e < cnt;
             const uint32_t d = valid ? digit_of(tk[e], shift, mask) : SIGMA;
-            const unsigned peers = peer_mask<DB>(d, valid);
+            unsigned peers;
+            if constexpr (C::PTAB) {
+                unsigned *pt = ptab + warp * SIGMA;
+                if (valid)
+                    atomicOr(&pt[d], 1u << lane);
+                __syncwarp();
+                peers = valid ? pt[d] : 0u;
+                __syncwarp();
+                if (valid && (__ffs(peers) - 1) == lane)
+                    pt[d] = 0u;
+            } else {
+                peers = peer_mask<DB>(d, valid);
+            }
             uint32_t base = 0;
             if (valid) {
                 base = hw[d];

@@ -121,14 +121,13 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES> struct R
     static constexpr int ITEMS = R / 32;     // elements per consumer thread
     static_assert(R % 32 == 0, "warp range must be a multiple of 32");
     static_assert(THREADS <= 1024, "one CTA holds at most 1024 threads");
-    // column scan over the warps' counts: TPB threads per bucket, in
-    // different warps (consecutive lanes take consecutive buckets)
-    static constexpr int TPB = NT >= 2 * SIGMA ? 2 : 1;
+    // column scan over the warps' counts: TPB adjacent lanes per bucket
+    static constexpr int TPB = NW >= 16 ? 4 : (NW >= 4 ? 2 : 1);
     static_assert(NW % TPB == 0, "rows split evenly");
-    // sigma <= 256: a per-warp 64-bit table per digit holds (running count
-    // << 32 | lane mask); shared-memory atomicOr builds the mask, far cheaper
-    // here than __match_any_sync or a ballot per digit bit.  sigma = 2048:
-    // ballot-per-bit masks and a 16-bit count table.
+    // sigma <= 256: a per-warp table of 32-bit lane masks by digit, built
+    // with shared-memory atomicOr (far cheaper here than __match_any_sync or
+    // a ballot per digit bit); sigma = 2048: ballot-per-bit masks.  Either
+    // way a per-warp 16-bit table keeps the running count of each digit.
     static constexpr bool PTAB = DB <= 8;
     // 32-bit key + 32-bit value: the in-place reorder writes (key, value)
     // pairs as one 8-byte word
@@ -140,10 +139,10 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES> struct R
     static constexpr size_t o_stage = 0;
     static constexpr size_t o_hist = o_stage + STAGES * STAGE;
     static constexpr size_t o_tab = o_hist + al(size_t(NW) * HROW * 2);
-    static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * SIGMA * 8) : 0);
+    static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * SIGMA * 4) : 0);
     static constexpr int NBK = 8; // tcnt, bstart, fill, cur, ccnt, nb, nbase, ncur
     static constexpr size_t o_psum = o_bk + al(size_t(NBK) * SIGMA * 4);
-    static constexpr size_t o_qb = o_psum + al(size_t(TPB) * SIGMA * 4);
+    static constexpr size_t o_qb = o_psum;
     static constexpr int LIST = 2 * SIGMA + MAXM + 1;
     // sigma <= 256: the block lists hold key/value pointers; sigma = 2048
     // (shared memory is tight): block indices
@@ -238,12 +237,11 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
     constexpr uint32_t SB = 32 - DB; // UC: bucket in the top DB bits, sequence below
     extern __shared__ __align__(128) unsigned char sm[];
     uint16_t *hist = reinterpret_cast<uint16_t *>(sm + C::o_hist);
-    unsigned long long *tab = reinterpret_cast<unsigned long long *>(sm + C::o_tab);
+    unsigned *ptab = reinterpret_cast<unsigned *>(sm + C::o_tab);
     uint32_t *bk = reinterpret_cast<uint32_t *>(sm + C::o_bk);
     uint32_t *tcnt = bk, *bstart = bk + SIGMA, *fill = bk + 2 * SIGMA, *cur = bk + 3 * SIGMA;
     uint32_t *ccnt = bk + 4 * SIGMA, *nb = bk + 5 * SIGMA, *nbase = bk + 6 * SIGMA;
     uint32_t *ncur = bk + 7 * SIGMA;
-    uint32_t *psum = reinterpret_cast<uint32_t *>(sm + C::o_psum);
     // per bucket: (chain offset of the tile's first element minus its start
     // in the reordered tile, index of the bucket's open block in the lists)
     uint2 *qb = reinterpret_cast<uint2 *>(sm + C::o_qb);
@@ -390,6 +388,9 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         ccnt[c] = 1;
         a.UC[q * SIGMA + c] = (uint32_t(c) << SB);
     }
+    if constexpr (C::PTAB)
+        for (int i = tid; i < NW * SIGMA; i += NT)
+            ptab[i] = 0u;
     uint32_t alloc = SIGMA; // i_out as a free-list index
     uint32_t fl0 = SIGMA;   // free-list index of flbuf[0]
     uint32_t pfv = 0;
@@ -430,35 +431,34 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
             dig[it] = valid ? digit_of(key[it], a.shift, mask) : uint32_t(SIGMA);
         }
         const unsigned lt = lanemask_lt();
+        uint16_t *hw = hist + warp * C::HROW;
+        for (int c = lane; c < SIGMA; c += 32)
+            hw[c] = 0;
         if constexpr (C::PTAB) {
             // row by row: lanes with the same digit OR their bit into the
-            // digit's table word and read back (count << 32 | lanes); the
-            // lowest of those lanes stores the advanced count with an empty
-            // lane mask.  Each warp zeroes its row first.
-            unsigned long long *tw = tab + warp * SIGMA;
-            for (int c = lane; c < SIGMA; c += 32)
-                tw[c] = 0ull;
+            // digit's mask word, read back the mask and the warp's running
+            // count; the lowest of those lanes advances the count and clears
+            // the word (the mask table is all zero between rows)
+            unsigned *pt = ptab + warp * SIGMA;
             __syncwarp();
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it) {
                 const uint32_t d = dig[it];
                 const bool v = d < SIGMA;
                 if (v)
-                    atomicOr(&tw[d], 1ull << lane);
+                    atomicOr(&pt[d], 1u << lane);
                 __syncwarp();
-                const unsigned long long ent = v ? tw[d] : 0ull;
-                const unsigned pm = static_cast<unsigned>(ent);
-                const uint32_t base = static_cast<uint32_t>(ent >> 32);
+                const unsigned pm = v ? pt[d] : 0u;
+                const uint32_t base = v ? hw[d] : 0u;
                 rk[it] = base + __popc(pm & lt);
                 __syncwarp();
-                if (v && (__ffs(pm) - 1) == lane)
-                    tw[d] = static_cast<unsigned long long>(base + __popc(pm)) << 32;
+                if (v && (__ffs(pm) - 1) == lane) {
+                    hw[d] = static_cast<uint16_t>(base + __popc(pm));
+                    pt[d] = 0u;
+                }
                 __syncwarp();
             }
         } else {
-            uint16_t *hw = hist + warp * C::HROW;
-            for (int c = lane; c < SIGMA; c += 32)
-                hw[c] = 0;
             unsigned peers[C::ITEMS];
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it)
@@ -479,45 +479,37 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
         }
         named_bar(1, NT);
 
-        // ---- 2. per-bucket warp offsets (exclusive over warps) and tile counts
-        {
+        // ---- 2. per-bucket warp offsets (exclusive over warps) and tile counts:
+        // TPB adjacent lanes share a bucket, each scanning NW/TPB warp rows
+        // (rows are padded so that these accesses are free of bank conflicts)
+        for (int t = tid; t < SIGMA * C::TPB; t += NT) {
+            const int c = t / C::TPB, part = t % C::TPB;
             constexpr int RPT = NW / C::TPB;
-            auto count = [&](int w, int c) -> uint32_t {
-                if constexpr (C::PTAB)
-                    return static_cast<uint32_t>(tab[w * SIGMA + c] >> 32);
-                else
-                    return hist[w * C::HROW + c];
-            };
-            for (int t = tid; t < SIGMA * C::TPB; t += NT) {
-                const int c = t % SIGMA, part = t / SIGMA;
-                uint32_t sum = 0;
+            uint32_t h[RPT], sum = 0;
 #pragma unroll
-                for (int r = 0; r < RPT; ++r)
-                    sum += count(part * RPT + r, c);
-                psum[part * SIGMA + c] = sum;
+            for (int r = 0; r < RPT; ++r) {
+                h[r] = hist[(part * RPT + r) * C::HROW + c];
+                sum += h[r];
             }
-            named_bar(1, NT);
-            for (int t = tid; t < SIGMA * C::TPB; t += NT) {
-                const int c = t % SIGMA, part = t / SIGMA;
-                uint32_t run = 0;
+            uint32_t incl = sum;
 #pragma unroll
-                for (int pp = 0; pp < C::TPB; ++pp)
-                    if (pp < part)
-                        run += psum[pp * SIGMA + c];
+            for (int o = 1; o < C::TPB; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o, C::TPB);
+                if (part >= o)
+                    incl += x;
+            }
+            uint32_t run = incl - sum;
 #pragma unroll
-                for (int r = 0; r < RPT; ++r) {
-                    const int w = part * RPT + r;
-                    const uint32_t h = count(w, c);
-                    hist[w * C::HROW + c] = static_cast<uint16_t>(run);
-                    run += h;
-                }
-                if (part == C::TPB - 1) {
-                    tcnt[c] = run;
-                    bstart[c] = run;
-                    const uint32_t fnew = fill[c] + run;
-                    nb[c] = fnew >> a.lb; // blocks filled -> new blocks (eager, Alg. 5)
-                    nbase[c] = fnew >> a.lb;
-                }
+            for (int r = 0; r < RPT; ++r) {
+                hist[(part * RPT + r) * C::HROW + c] = static_cast<uint16_t>(run);
+                run += h[r];
+            }
+            if (part == C::TPB - 1) {
+                tcnt[c] = incl;
+                bstart[c] = incl;
+                const uint32_t fnew = fill[c] + incl;
+                nb[c] = fnew >> a.lb; // blocks filled -> new blocks (eager, Alg. 5)
+                nbase[c] = fnew >> a.lb;
             }
         }
         named_bar(1, NT);
