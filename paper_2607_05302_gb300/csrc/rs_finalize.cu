@@ -155,8 +155,13 @@ __global__ void k_fz_edges(FinArgs a)
 // mode 0: val = minimum position of the window; mode 1: val = window length.
 // Each thread only rewrites its own entry, and any neighbour value it reads
 // is a valid window, so asynchronous updates only speed convergence.
-__global__ void k_fz_jump(unsigned long long *jump, uint32_t npi, int mode)
+__global__ void k_fz_jump(unsigned long long *jump, uint32_t npi, int mode, uint32_t *changes,
+                          int round)
 {
+    // once a round changed nothing the entries are final: later rounds exit
+    if (round > 0 && *(volatile uint32_t *)&changes[round - 1] == 0)
+        return;
+    bool changed = false;
     for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npi; x += gridDim.x * blockDim.x) {
         const unsigned long long e = ld64(&jump[x]);
         const uint32_t v = hi32(e);
@@ -166,8 +171,14 @@ __global__ void k_fz_jump(unsigned long long *jump, uint32_t npi, int mode)
         const uint32_t fv = hi32(f);
         if (fv == ABS)
             continue; // x's window already ends at an absorbing entry
-        st64(&jump[x], pk(lo32(f), mode == 0 ? min(v, fv) : v + fv));
+        const unsigned long long ne = pk(lo32(f), mode == 0 ? min(v, fv) : v + fv);
+        if (ne != e) {
+            st64(&jump[x], ne);
+            changed = true;
+        }
     }
+    if (__syncthreads_or(changed) && threadIdx.x == 0)
+        atomicAdd(&changes[round], 1u);
 }
 
 // classify each moving block in pi's top bits: moving / on a cycle / the
@@ -511,9 +522,14 @@ __device__ __forceinline__ uint32_t partials_before(const FinArgs &a, uint32_t n
     return l;
 }
 
-// per window: first source block, partials before it, the earliest window
-// that reads from this window's destinations, and whether it is in place
-__global__ void k_fz_winplan(FinArgs a, uint4 *plan)
+// Per window: first source block and the partials before it, the earliest
+// window that reads from this window's destinations, whether it is in place,
+// and up to MAXSEG runs of constant shift (between partial blocks the source
+// of destination x is x + D, in A, or x + D - nA*b in T).
+constexpr int MAXSEG = 4;
+enum { WP_INPLACE = 1u, WP_SEGS = 2u };
+
+__global__ void k_fz_winplan(FinArgs a, uint4 *plan, uint4 *segs)
 {
     const uint32_t nP = a.state[ST_NP];
     const unsigned long long n = a.n;
@@ -526,7 +542,7 @@ __global__ void k_fz_winplan(FinArgs a, uint4 *plan)
         block_of(a, nP, x0 + cnt - 1, qe, jpe);
         // in place iff no partial block precedes the last block and it is in
         // A: every source is then its own destination
-        const uint32_t inplace = (qe < a.nA && a.D[jpe] == 0) ? 1u : 0u;
+        uint32_t flags = (qe < a.nA && a.D[jpe] == 0) ? WP_INPLACE : 0u;
         // the destination of the element at virtual position x0 is the
         // smallest destination among sources inside [x0, x0 + W)
         const uint32_t qv = static_cast<uint32_t>(x0 / a.b);
@@ -536,12 +552,40 @@ __global__ void k_fz_winplan(FinArgs a, uint4 *plan)
             const unsigned long long offv = (unsigned long long)qv * a.b - a.D[j];
             wlo = static_cast<uint32_t>(offv / a.W);
         }
-        plan[w] = make_uint4(q0, jp0, wlo, inplace);
+        // constant-shift runs
+        const unsigned long long end = x0 + cnt, nAb = (unsigned long long)a.nA * a.b;
+        unsigned long long x = x0;
+        uint32_t k = 0;
+        while (x < end && k < MAXSEG) {
+            uint32_t q, jp;
+            block_of(a, nP, x, q, jp);
+            const unsigned long long g = a.D[jp];
+            unsigned long long se = end;
+            bool part_after_A = true;
+            if (jp < nP) {
+                const uint2 pj = a.P[jp];
+                const unsigned long long endp = (unsigned long long)(pj.x - a.H) * a.b - g + pj.y;
+                se = min(se, endp);
+                part_after_A = pj.x - a.H >= a.nA;
+            }
+            const bool inT = q >= a.nA;
+            if (!inT && part_after_A)
+                se = min(se, nAb - g); // the run of A blocks ends at block nA
+            const unsigned long long src = x + g - (inT ? nAb : 0ull);
+            segs[size_t(w) * MAXSEG + k] =
+                make_uint4(static_cast<uint32_t>(x - x0), static_cast<uint32_t>(se - x),
+                           static_cast<uint32_t>(src), static_cast<uint32_t>(src >> 32) | (inT ? 0x80000000u : 0u));
+            x = se;
+            ++k;
+        }
+        if (x >= end)
+            flags |= WP_SEGS | (k << 8);
+        plan[w] = make_uint4(q0, jp0, wlo, flags);
     }
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *plan)
+__global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *plan, const uint4 *segs)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
     KT *wk = reinterpret_cast<KT *>(fsm);
@@ -568,7 +612,26 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
         const uint4 pl = s_plan;
         const unsigned long long x0 = (unsigned long long)w * a.W;
         const uint32_t cnt = static_cast<uint32_t>(min((unsigned long long)a.W, n - x0));
-        if (!pl.w) {
+        const bool inplace = (pl.w & WP_INPLACE) != 0;
+        if (!inplace && (pl.w & WP_SEGS)) {
+            // constant-shift runs: plain strided copies, several loads in flight
+            const uint32_t nseg = (pl.w >> 8) & 0xFF;
+            for (uint32_t k = 0; k < nseg; ++k) {
+                const uint4 sg = segs[size_t(w) * MAXSEG + k];
+                const unsigned long long src = sg.z | ((unsigned long long)(sg.w & 0x7FFFFFFFu) << 32);
+                const bool inT = (sg.w & 0x80000000u) != 0;
+                const KT *sk = (inT ? static_cast<const KT *>(a.Tk) : static_cast<const KT *>(a.Ak)) + src;
+#pragma unroll 8
+                for (uint32_t i = threadIdx.x; i < sg.y; i += blockDim.x)
+                    wk[sg.x + i] = sk[i];
+                if (hv) {
+                    const uint32_t *sv = (inT ? a.Tv : a.Av) + src;
+#pragma unroll 8
+                    for (uint32_t i = threadIdx.x; i < sg.y; i += blockDim.x)
+                        wv[sg.x + i] = sv[i];
+                }
+            }
+        } else if (!inplace) {
             // read phase: the blocks covering destinations [x0, x0+cnt)
             uint32_t q = pl.x, jp = pl.y;
             unsigned long long off = (unsigned long long)q * a.b - a.D[jp];
@@ -601,7 +664,7 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
             __threadfence();
             st_release(&a.wflag[w], 1u);
         }
-        if (!pl.w) {
+        if (!inplace) {
             // wait for every earlier window that reads from our destinations
             for (uint32_t v = pl.z + threadIdx.x; v < w; v += blockDim.x)
                 wait_flag(&a.wflag[v]);
@@ -617,7 +680,7 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
 }
 
 struct FinLayout {
-    size_t ctr, sflag, wflag, slotflag, rec, wplan, slotk, slotv, total;
+    size_t ctr, sflag, wflag, slotflag, rec, wplan, wsegs, slotk, slotv, total;
     uint32_t K, W, nstr, nwin, nrec, nslots;
 };
 
@@ -639,7 +702,7 @@ FinLayout fin_layout(const Geom &g)
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     L.ctr = off;
-    off += al(C_WORDS * 4);
+    off += al((C_WORDS + 128) * 4); // counters, then the jump rounds' change counts
     L.sflag = off;
     off += al(size_t(L.nstr) * 4);
     L.wflag = off;
@@ -650,6 +713,8 @@ FinLayout fin_layout(const Geom &g)
     off += al(size_t(L.nrec) * 16);
     L.wplan = off;
     off += al(size_t(L.nwin) * 16);
+    L.wsegs = off;
+    off += al(size_t(L.nwin) * 16 * MAXSEG);
     L.slotk = off;
     off += al(size_t(L.nslots) * g.b * g.kb);
     L.slotv = off;
@@ -710,13 +775,14 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     rounds += 1;
     k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
     k_fz_edges<<<grid, FIN_T, 0, st>>>(a);
+    uint32_t *chg = a.ctr + C_WORDS; // per-round change counters (cleared with the flags)
     for (int r = 0; r < rounds; ++r)
-        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 0);
+        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 0, chg, r);
     k_fz_classify<<<grid, FIN_T, 0, st>>>(a);
     k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
     k_fz_rank_edges<<<grid, FIN_T, 0, st>>>(a);
     for (int r = 0; r < rounds; ++r)
-        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 1);
+        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 1, chg + 64, r);
     k_fz_chains<<<grid, FIN_T, 0, st>>>(a);
     k_fz_order<<<grid, FIN_T, 0, st>>>(a);
     const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
@@ -736,9 +802,10 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     k_fz_move<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, msm, st>>>(a);
     k_fz_move_deferred<KT><<<sms, FIN_T, msm, st>>>(a);
     uint4 *wplan = reinterpret_cast<uint4 *>(base + L.wplan);
-    k_fz_winplan<<<(L.nwin + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, wplan);
+    uint4 *wsegs = reinterpret_cast<uint4 *>(base + L.wsegs);
+    k_fz_winplan<<<(L.nwin + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, wplan, wsegs);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_compact<KT>, FIN_T, csm);
-    k_fz_compact<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, csm, st>>>(a, wplan);
+    k_fz_compact<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, csm, st>>>(a, wplan, wsegs);
     g_launches += 11 + 2 * rounds;
     return cudaGetLastError();
 }
