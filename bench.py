@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--num-chunks", type=int, default=0)
     ap.add_argument("--no-oop", action="store_true", help="skip the out-of-place comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -157,6 +158,45 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def end_to_end(a, R, keys0, vals0, dk, dv, n, kb, db, E, world, barrier, stream):
+    """Same metric through the public call radsort_sort with pinned host
+    buffers: H2D of the inputs, the sort, D2H of the result, every step."""
+    import ctypes
+
+    import torch
+
+    ktype = keys0.dtype
+    hk = torch.empty(n, dtype=ktype, pin_memory=True)
+    hv = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hk.copy_(keys0.cpu())
+    hv.copy_(vals0.cpu())
+    ok_ = torch.empty_like(hk, pin_memory=True)
+    ov_ = torch.empty_like(hv, pin_memory=True)
+    steps = max(2, min(a.steps, 5))
+
+    def step():
+        dk.copy_(hk, non_blocking=True)
+        dv.copy_(hv, non_blocking=True)
+        R.radsort_sort(ctypes.c_void_p(dk.data_ptr()), ctypes.c_void_p(dv.data_ptr()), n, kb, db,
+                       R._torch_stream(None))
+        ok_.copy_(dk, non_blocking=True)
+        ov_.copy_(dv, non_blocking=True)
+
+    step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1) / steps
+    R.radsort_device_status()
+    return {"value": world * n / (ms / 1e3) / 1e9, "unit": "Gkeys/s",
+            "h2d_bytes_per_step": n * E, "d2h_bytes_per_step": n * E, "steps": steps,
+            "call": "radsort_sort (automatic plan, allocating, stream-ordered) with pinned host buffers"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -287,41 +327,9 @@ def main():
     step_bytes = n * (4 * 2 * E) if kb == 4 and db == 8 else None
 
     # ---- end to end through the public call with host buffers
-    hk = torch.empty(n, dtype=ktype, pin_memory=True)
-    hv = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    hk.copy_(keys0.cpu())
-    hv.copy_(vals0.cpu())
-    ok_ = torch.empty_like(hk, pin_memory=True)
-    ov_ = torch.empty_like(hv, pin_memory=True)
-    dk, dv = kbufs[0], vbufs[0]
-    e2e_steps = max(2, min(a.steps, 5))
-
-    def e2e_step():
-        dk.copy_(hk, non_blocking=True)
-        dv.copy_(hv, non_blocking=True)
-        R.radsort_sort(ctypes_ptr(dk), ctypes_ptr(dv), n, kb, db, R._torch_stream(None))
-        ok_.copy_(dk, non_blocking=True)
-        ov_.copy_(dv, non_blocking=True)
-
-    import ctypes
-
-    def ctypes_ptr(t):
-        return ctypes.c_void_p(t.data_ptr())
-
-    e2e_step()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    R.radsort_device_status()
-    e2e = {"value": world * n / (e2e_ms / 1e3) / 1e9, "unit": "Gkeys/s",
-           "h2d_bytes_per_step": n * E, "d2h_bytes_per_step": n * E, "steps": e2e_steps,
-           "call": "radsort_sort (allocating, stream-ordered) with pinned host buffers"}
-    del hk, hv, ok_, ov_
+    e2e = None
+    if not a.no_e2e:
+        e2e = end_to_end(a, R, keys0, vals0, kbufs[0], vbufs[0], n, kb, db, E, world, barrier, stream)
 
     # ---- out-of-place comparator on the same data and GPU
     oop = None

@@ -111,6 +111,19 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// TMA bulk store shared -> global (bulk-group completion)
+__device__ __forceinline__ void bulk_s2g(void *dst_gmem, const void *src_smem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_u32(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of this thread's bulk stores have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // bounded wait until *p != 0
 __device__ __forceinline__ bool wait_flag(const uint32_t *p)
 {
@@ -326,10 +339,19 @@ __global__ void __launch_bounds__(FIN_T) k_fz_move(FinArgs a)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
     __shared__ uint32_t s_ticket, s_src[MAXK], s_dst[MAXK], s_kind[MAXK], s_slot[MAXK], s_save[MAXK];
-    __shared__ uint32_t s_wait, s_any2;
+    __shared__ uint32_t s_wait, s_bytes;
+    __shared__ __align__(8) uint64_t s_bar;
     const BlockIO<KT> io(a);
     const uint32_t total = a.ctr[C_ORDER];
     const uint32_t nstr = (total + a.K - 1) / a.K;
+    const uint32_t kbytes = a.b * sizeof(KT), vbytes = a.Av ? a.b * 4 : 0;
+    const uint32_t bbytes = kbytes + vbytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0)
             s_ticket = atomicAdd(&a.ctr[C_STRIDE], 1u);
@@ -378,42 +400,68 @@ __global__ void __launch_bounds__(FIN_T) k_fz_move(FinArgs a)
             s_wait = (t > 0 && !(o & O_FIRST) && !(o & O_DEFER)) ? 1u : 0u;
         }
         __syncthreads();
-        // read phase: every source block into shared memory; heads to slots
-        for (uint32_t idx = threadIdx.x; idx < cnt * io.nvec; idx += blockDim.x) {
-            const uint32_t i = idx / io.nvec, v = idx - i * io.nvec;
-            if (s_kind[i] == 1)
-                io.sbuf(fsm, i)[v] = *io.gvec(s_src[i], v);
-            if (s_save[i] != SLOT_NONE)
-                *io.slotvec(s_save[i], v) = *io.gvec(s_dst[i], v);
+        // read phase: every source block into shared memory by TMA bulk
+        // copies (warp 0, one entry per lane); heads of straddling cycles to
+        // their slots with plain copies
+        if (threadIdx.x < 32) {
+            const uint32_t i = threadIdx.x;
+            const bool mv = i < cnt && s_kind[i] == 1;
+            const uint32_t tot = warp_sum(mv ? bbytes : 0u);
+            if (i == 0)
+                s_bytes = tot;
+            if (i == 0 && tot)
+                mbar_arrive_expect_tx(&s_bar, tot);
+            __syncwarp();
+            if (mv) {
+                unsigned char *buf = fsm + size_t(i) * bbytes;
+                bulk_g2s(buf, kblk<KT>(a, s_src[i]), kbytes, &s_bar);
+                if (vbytes)
+                    bulk_g2s(buf + kbytes, vblk(a, s_src[i]), vbytes, &s_bar);
+            }
         }
+        for (uint32_t i = 0; i < cnt; ++i)
+            if (s_save[i] != SLOT_NONE)
+                for (uint32_t v = threadIdx.x; v < io.nvec; v += blockDim.x)
+                    *io.slotvec(s_save[i], v) = *io.gvec(s_dst[i], v);
         __syncthreads();
+        if (s_bytes) {
+            mbar_wait(&s_bar, phase);
+            phase ^= 1u;
+        }
         if (threadIdx.x == 0) {
             __threadfence();
-            uint32_t any2 = 0;
-            for (uint32_t i = 0; i < cnt; ++i) {
+            for (uint32_t i = 0; i < cnt; ++i)
                 if (s_save[i] != SLOT_NONE)
                     st_release(&a.slot_flag[s_save[i]], 1u);
-                any2 |= s_kind[i] == 2;
-            }
             st_release(&a.sflag[t], 1u);
             if (s_wait)
                 wait_flag(&a.sflag[t - 1]);
             for (uint32_t i = 0; i < cnt; ++i)
                 if (s_kind[i] == 2)
                     wait_flag(&a.slot_flag[s_slot[i]]);
-            s_any2 = any2;
         }
         __syncthreads();
-        // write phase
-        for (uint32_t idx = threadIdx.x; idx < cnt * io.nvec; idx += blockDim.x) {
-            const uint32_t i = idx / io.nvec, v = idx - i * io.nvec;
-            if (s_kind[i] == 1)
-                *io.gvec(s_dst[i], v) = io.sbuf(fsm, i)[v];
-            else if (s_kind[i] == 2)
-                *io.gvec(s_dst[i], v) = *io.slotvec(s_slot[i], v);
+        // write phase: bulk stores from shared memory; closing writes from slots
+        if (threadIdx.x < 32) {
+            const uint32_t i = threadIdx.x;
+            if (i < cnt && s_kind[i] == 1) {
+                const unsigned char *buf = fsm + size_t(i) * bbytes;
+                bulk_s2g(kblk<KT>(a, s_dst[i]), buf, kbytes);
+                if (vbytes)
+                    bulk_s2g(vblk(a, s_dst[i]), buf + kbytes, vbytes);
+            }
+            bulk_commit();
         }
+        for (uint32_t i = 0; i < cnt; ++i)
+            if (s_kind[i] == 2)
+                for (uint32_t v = threadIdx.x; v < io.nvec; v += blockDim.x)
+                    *io.gvec(s_dst[i], v) = *io.slotvec(s_slot[i], v);
+        if (threadIdx.x < 32)
+            bulk_wait_read(); // shared buffers free for the next stride
         __syncthreads();
     }
+    if (threadIdx.x < 32)
+        bulk_wait_all();
 }
 
 // straddling cycles beyond the slot capacity: one CTA moves a whole cycle,
@@ -588,10 +636,22 @@ template <typename KT>
 __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *plan, const uint4 *segs)
 {
     extern __shared__ __align__(16) unsigned char fsm[];
+    // keys: W elements plus 16 bytes of slack per run; values likewise
+    constexpr uint32_t KA = 16 / sizeof(KT); // elements per 16 bytes
+    // each run's 16-byte-aligned superset adds at most 2*KA-2 elements
+    const uint32_t kcap = a.W + 2 * KA * (MAXSEG + 1), vcap = a.W + 8 * (MAXSEG + 1);
     KT *wk = reinterpret_cast<KT *>(fsm);
-    uint32_t *wv = reinterpret_cast<uint32_t *>(fsm + size_t(a.W) * sizeof(KT));
+    uint32_t *wv = reinterpret_cast<uint32_t *>(fsm + ((size_t(kcap) * sizeof(KT) + 15) & ~size_t(15)));
     __shared__ uint32_t s_ticket;
     __shared__ uint4 s_plan;
+    __shared__ uint32_t s_kb[MAXSEG], s_vb[MAXSEG]; // smem start of each run (incl. lead)
+    __shared__ __align__(8) uint64_t s_bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
     const uint32_t nP = a.state[ST_NP];
     const uint32_t NL = a.state[ST_F] - a.H;
     const unsigned long long n = a.n;
@@ -610,26 +670,60 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
         if (w >= nwin)
             break;
         const uint4 pl = s_plan;
+        __syncthreads(); // everyone has read s_ticket before it is reused below
         const unsigned long long x0 = (unsigned long long)w * a.W;
         const uint32_t cnt = static_cast<uint32_t>(min((unsigned long long)a.W, n - x0));
         const bool inplace = (pl.w & WP_INPLACE) != 0;
-        if (!inplace && (pl.w & WP_SEGS)) {
-            // constant-shift runs: plain strided copies, several loads in flight
-            const uint32_t nseg = (pl.w >> 8) & 0xFF;
-            for (uint32_t k = 0; k < nseg; ++k) {
-                const uint4 sg = segs[size_t(w) * MAXSEG + k];
-                const unsigned long long src = sg.z | ((unsigned long long)(sg.w & 0x7FFFFFFFu) << 32);
-                const bool inT = (sg.w & 0x80000000u) != 0;
-                const KT *sk = (inT ? static_cast<const KT *>(a.Tk) : static_cast<const KT *>(a.Ak)) + src;
-#pragma unroll 8
-                for (uint32_t i = threadIdx.x; i < sg.y; i += blockDim.x)
-                    wk[sg.x + i] = sk[i];
-                if (hv) {
-                    const uint32_t *sv = (inT ? a.Tv : a.Av) + src;
-#pragma unroll 8
-                    for (uint32_t i = threadIdx.x; i < sg.y; i += blockDim.x)
-                        wv[sg.x + i] = sv[i];
+        const bool segmode = !inplace && (pl.w & WP_SEGS);
+        const uint32_t nseg = segmode ? (pl.w >> 8) & 0xFF : 0u;
+        if (segmode) {
+            // constant-shift runs: one TMA bulk load per run (keys, values) of
+            // the 16-byte-aligned superset of its source; the lead is skipped
+            // when writing.  The superset stays inside its region of A or T,
+            // whose ends are multiples of the block size.
+            if (threadIdx.x == 0) {
+                uint32_t kpos = 0, vpos = 0, bytes = 0;
+                uint32_t kb[MAXSEG], vb[MAXSEG];
+                unsigned long long ks0[MAXSEG], vs0[MAXSEG];
+                uint32_t kn[MAXSEG], vn[MAXSEG];
+                bool kt[MAXSEG];
+                for (uint32_t k = 0; k < nseg; ++k) {
+                    const uint4 sg = segs[size_t(w) * MAXSEG + k];
+                    const unsigned long long src = sg.z | ((unsigned long long)(sg.w & 0x7FFFFFFFu) << 32);
+                    kt[k] = (sg.w & 0x80000000u) != 0;
+                    ks0[k] = src & ~(unsigned long long)(KA - 1);
+                    const uint32_t klead = static_cast<uint32_t>(src - ks0[k]);
+                    kn[k] = (klead + sg.y + KA - 1) & ~(KA - 1);
+                    kb[k] = kpos;
+                    s_kb[k] = kpos + klead;
+                    kpos += kn[k];
+                    bytes += kn[k] * sizeof(KT);
+                    if (hv) {
+                        vs0[k] = src & ~3ull;
+                        const uint32_t vlead = static_cast<uint32_t>(src - vs0[k]);
+                        vn[k] = (vlead + sg.y + 3) & ~3u;
+                        vb[k] = vpos;
+                        s_vb[k] = vpos + vlead;
+                        vpos += vn[k];
+                        bytes += vn[k] * 4;
+                    }
                 }
+                if (bytes) {
+                    mbar_arrive_expect_tx(&s_bar, bytes);
+                    for (uint32_t k = 0; k < nseg; ++k) {
+                        const KT *sk = (kt[k] ? static_cast<const KT *>(a.Tk) : static_cast<const KT *>(a.Ak)) + ks0[k];
+                        if (kn[k])
+                            bulk_g2s(wk + kb[k], sk, kn[k] * sizeof(KT), &s_bar);
+                        if (hv && vn[k])
+                            bulk_g2s(wv + vb[k], (kt[k] ? a.Tv : a.Av) + vs0[k], vn[k] * 4, &s_bar);
+                    }
+                }
+                s_ticket = bytes; // reuse: nonzero when a phase was armed
+            }
+            __syncthreads();
+            if (s_ticket) {
+                mbar_wait(&s_bar, phase);
+                phase ^= 1u;
             }
         } else if (!inplace) {
             // read phase: the blocks covering destinations [x0, x0+cnt)
@@ -669,10 +763,28 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
             for (uint32_t v = pl.z + threadIdx.x; v < w; v += blockDim.x)
                 wait_flag(&a.wflag[v]);
             __syncthreads();
-            for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-                Ak[x0 + i] = wk[i];
-                if (hv)
-                    a.Av[x0 + i] = wv[i];
+            if (segmode) {
+                for (uint32_t k = 0; k < nseg; ++k) {
+                    const uint4 sg = segs[size_t(w) * MAXSEG + k];
+                    const KT *sk = wk + s_kb[k];
+                    KT *dk = Ak + x0 + sg.x;
+#pragma unroll 4
+                    for (uint32_t i = threadIdx.x; i < sg.y; i += blockDim.x)
+                        dk[i] = sk[i];
+                    if (hv) {
+                        const uint32_t *sv = wv + s_vb[k];
+                        uint32_t *dv = a.Av + x0 + sg.x;
+#pragma unroll 4
+                        for (uint32_t i = threadIdx.x; i < sg.y; i += blockDim.x)
+                            dv[i] = sv[i];
+                    }
+                }
+            } else {
+                for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+                    Ak[x0 + i] = wk[i];
+                    if (hv)
+                        a.Av[x0 + i] = wv[i];
+                }
             }
         }
         __syncthreads();
@@ -689,8 +801,8 @@ FinLayout fin_layout(const Geom &g)
     FinLayout L{};
     const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
     uint32_t K = static_cast<uint32_t>((64u << 10) / bbytes);
-    if (K > MAXK)
-        K = MAXK;
+    if (K > 32)
+        K = 32; // one warp issues the bulk copies, one entry per lane
     if (K < 2)
         K = 2;
     L.K = K;
@@ -787,7 +899,8 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     k_fz_order<<<grid, FIN_T, 0, st>>>(a);
     const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
     const size_t msm = bbytes * L.K;
-    const size_t csm = size_t(L.W) * (g.kb + (g.hasv ? 4 : 0));
+    const size_t kcap = L.W + 2 * (16 / g.kb) * (MAXSEG + 1), vcap = L.W + 8 * (MAXSEG + 1);
+    const size_t csm = ((kcap * g.kb + 15) & ~size_t(15)) + (g.hasv ? vcap * 4 : 0);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_fz_move<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
