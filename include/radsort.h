@@ -121,6 +121,31 @@ radsort_status radsort_lsd_oop_sort(void *keys, uint32_t *values, void *keys_alt
                                     uint32_t *values_alt, size_t n, int key_bytes, int digit_bits,
                                     void *stream);
 
+/*
+ * radsort_sort_noalloc: radsort_sort without any device allocation.  The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * allocate device memory at the point of the call -- code running inside a
+ * framework that owns all device memory through its own pool, loops whose
+ * latency cannot absorb the implicit synchronisation and fragmentation of
+ * cudaMalloc, or error paths that run when memory is already exhausted.
+ *
+ * The workspace is a fixed array of RADSORT_NOALLOC_SCRATCH_BYTES compiled into
+ * the library (every GPU that loads the library holds it until the process
+ * exits).  The plan is block size 256 with as many chunks (up to one per SM)
+ * as fit; an n whose workspace does not fit even with one chunk returns
+ * RADSORT_ENOMEM and enqueues nothing (up to about 1.07e9 elements with
+ * 4-byte keys and values fit, 8.8e8 with 8-byte keys).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  No call allocates or frees memory.  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other host threads)
+ * race and corrupt each other; serialise them.  Each call rebuilds every
+ * part of the workspace it reads, so a previous call's leftovers do no harm.
+ */
+#define RADSORT_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+radsort_status radsort_sort_noalloc(void *keys, uint32_t *values, size_t n, int key_bytes,
+                                    int digit_bits, void *stream);
+
 /* Order-preserving bit transform for float32 keys, in place on the device:
  * inverse = 0 maps IEEE bits to unsigned-orderable bits, inverse = 1 back. */
 radsort_status radsort_float_keys(uint32_t *keys, size_t n, int inverse, void *stream);

@@ -415,6 +415,85 @@ radsort_status radsort_sort(void *keys, uint32_t *values, size_t n, int key_byte
                        nullptr, nullptr);
 }
 
+} // extern "C"
+
+// ---------------------------------------------------------------- no allocation
+// Scratch of radsort_sort_noalloc: one array in this library's device image.
+// Every GPU that loads the library holds these bytes until the process
+// exits.  Host code must never pass the symbol itself to a kernel: on the
+// host it names a stand-in, not device memory.  The device address is taken
+// with cudaGetSymbolAddress once per device, below.
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RADSORT_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// device address of the scratch on the current device (set up on first use)
+radsort_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return RADSORT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return e != cudaSuccess ? cuda_status(e) : RADSORT_ECUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return RADSORT_OK;
+}
+
+// block size 256 and as many chunks (up to one per SM) as fit in the scratch
+radsort_status noalloc_plan(size_t n, int kb, bool hasv, int db, radsort_plan *pl)
+{
+    std::memset(pl, 0, sizeof(*pl));
+    pl->block_size = 256;
+    uint32_t lo = 1, hi = static_cast<uint32_t>(num_sms());
+    Geom g;
+    if (fill_geom(n, kb, hasv, db, 256, 1, &g) != RADSORT_OK ||
+        layout(g, nullptr, nullptr) > RADSORT_NOALLOC_SCRATCH_BYTES)
+        return RADSORT_ENOMEM; // n too large for the fixed scratch
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (fill_geom(n, kb, hasv, db, 256, mid, &g) == RADSORT_OK &&
+            layout(g, nullptr, nullptr) <= RADSORT_NOALLOC_SCRATCH_BYTES)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    pl->num_chunks = lo;
+    return RADSORT_OK;
+}
+} // namespace
+
+extern "C" {
+
+radsort_status radsort_sort_noalloc(void *keys, uint32_t *values, size_t n, int key_bytes,
+                                    int digit_bits, void *stream)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (n <= 1)
+        return RADSORT_OK;
+    radsort_plan pl;
+    radsort_status s = noalloc_plan(n, key_bytes, values != nullptr, digit_bits, &pl);
+    if (s != RADSORT_OK)
+        return s;
+    void *ws = nullptr;
+    s = noalloc_scratch(&ws);
+    if (s != RADSORT_OK)
+        return s;
+    return sort_common(keys, values, n, key_bytes, digit_bits, 0, &pl, ws,
+                       RADSORT_NOALLOC_SCRATCH_BYTES, stream, -1, nullptr, nullptr);
+}
+
 radsort_status radsort_sort_rounds(void *keys, uint32_t *values, size_t n, int key_bytes,
                                    int digit_bits, int rounds, const radsort_plan *plan,
                                    void *out_keys, uint32_t *out_values, void *stream)

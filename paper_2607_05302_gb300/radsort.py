@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
             "radsort_plan_default": ([sz, i, i, i, pplan], i),
             "radsort_workspace_size": ([sz, i, i, i, pplan, ctypes.POINTER(sz)], i),
             "radsort_sort": ([vp, vp, sz, i, i, vp], i),
+            "radsort_sort_noalloc": ([vp, vp, sz, i, i, vp], i),
             "radsort_sort_ex": ([vp, vp, sz, i, i, u32, pplan, vp, sz, vp], i),
             "radsort_sort_rounds": ([vp, vp, sz, i, i, i, pplan, vp, vp, vp], i),
             "radsort_lsd_oop_sort": ([vp, vp, vp, vp, sz, i, i, vp], i),
@@ -76,6 +77,7 @@ def lib() -> ctypes.CDLL:
 
 # exported names declared in include/radsort.h
 EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_workspace_size", "radsort_sort",
+           "radsort_sort_noalloc",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort", "radsort_float_keys",
            "radsort_device_status", "radsort_trace_enable", "radsort_trace_read",
            "radsort_launch_count")
