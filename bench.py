@@ -160,6 +160,37 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def round_kernel_hash():
+    """Hash of the round kernel's source: a traffic figure taken with ncu on an
+    older kernel is not reported."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("rs_round.cu", "rs_common.cuh", "rs_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2607_05302_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n, kb, db):
+    """DRAM bytes per k_round launch (dram__bytes_read.sum + write.sum) from
+    the committed ncu summary, scaled from the captured size to n by the
+    elements processed; None if the summary is missing or older than the
+    kernel."""
+    path = os.path.join(ROOT, "profiles", "k_round_u32kv_d8_ncu.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    import re
+
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_element:\s*([0-9.]+)", txt)
+    if not m or not t or m.group(1) != round_kernel_hash() or kb != 4 or db != 8:
+        return None
+    return round(float(t.group(1)) * n)
+
+
 def end_to_end(a, R, keys0, vals0, dk, dv, n, kb, db, E, world, barrier, stream):
     """Same metric through the public call radsort_sort with pinned host
     buffers: H2D of the inputs, the sort, D2H of the result, every step."""
@@ -248,10 +279,11 @@ def main():
     vals0 = torch.arange(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    bs, pc = a.block_size, a.num_chunks
-    if not bs or not pc:
-        b0, p0 = R.radsort_plan_default(n, kb, 4, db)
-        bs, pc = bs or b0, pc or p0
+    # throughput plan: one chunk per SM, b = 256 (the 2% memory plan is timed
+    # beside it, see plan_2pct)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    bs = a.block_size or 256
+    pc = a.num_chunks or sms
     wsb = R.radsort_workspace_size(n, kb, 4, db, bs, pc)
     ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
 
@@ -319,12 +351,36 @@ def main():
     avg_round = statistics.mean(round_ms) if round_ms else float("nan")
     hbm, src = peaks()
     achieved = (n * 2 * E) / (avg_round / 1e3) / 1e9
+    traffic = profiled_traffic(n, kb, db)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None,
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "kernel": "k_round (sortPhase, Alg. 5)",
                 "algorithmic_bytes_per_launch": n * 2 * E, "peak_source": src,
                 "avg_launch_ms": round(avg_round, 4)}
     step_bytes = n * (4 * 2 * E) if kb == 4 and db == 8 else None
+
+    # ---- the 2% memory plan (automatic plan) on the same data
+    plan2 = None
+    if not a.no_oop:
+        b2, p2 = R.radsort_plan_default(n, kb, 4, db)
+        ws2 = R.radsort_workspace_size(n, kb, 4, db, b2, p2)
+        wst = torch.empty(max(ws2, 1), dtype=torch.uint8, device=dev)
+        for i in range(min(nbuf, 2)):
+            refill(i)
+        R.sort_tensors(kbufs[0], vbufs[0], digit_bits=db, block_size=b2, num_chunks=p2, workspace=wst)
+        barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        R.sort_tensors(kbufs[1 % nbuf], vbufs[1 % nbuf], digit_bits=db, block_size=b2, num_chunks=p2,
+                       workspace=wst)
+        q1.record(stream)
+        barrier()
+        R.radsort_device_status()
+        pms = q0.elapsed_time(q1)
+        plan2 = {"block_size": b2, "num_chunks": p2, "extra_bytes": ws2,
+                 "extra_frac": round(ws2 / (n * E), 5), "value": round(world * n / (pms / 1e3) / 1e9, 3),
+                 "unit": "Gkeys/s", "ms_per_step": round(pms, 3), "steps": 1}
+        del wst
 
     # ---- end to end through the public call with host buffers
     e2e = None
@@ -379,7 +435,7 @@ def main():
                        "l2": "inputs larger than L2: each timed step sorts its own fresh 2^%d-element copy" % a.log2n},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
-            "oop": oop,
+            "oop": oop, "plan_2pct": plan2,
             "phases_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
             "algorithmic_bytes_per_step": step_bytes,
         }

@@ -169,15 +169,22 @@ def check_sorted_stable_perm(orig_keys_t, keys_t, vals_t, key_bits):
     assert bool((v[1:][eq] > v[:-1][eq]).all())
 
 
+def bench_plan():
+    """The launch configuration bench.py times: b = 256, one chunk per SM."""
+    return 256, torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("plan", ["auto", "bench"])
 @pytest.mark.parametrize("dist", ["uniform", "zipf", "equal", "sorted", "reverse"])
-def test_full_size_2p28_properties(dist):
-    """n = 2^28 uint32 keys + index payload, automatic plan (the bench's launch
-    configuration)."""
+def test_full_size_2p28_properties(dist, plan):
+    """n = 2^28 uint32 keys + index payload, in the automatic (2% memory) plan
+    and in the bench's launch configuration."""
     n = 1 << 28
     keys = torch.from_numpy(W.make_keys(dist, n).view(np.int32)).to(DEV)
     vals = torch.arange(n, dtype=torch.int32, device=DEV)
     kt = keys.clone()
-    R.sort_tensors(kt, vals)
+    bs, pc = bench_plan() if plan == "bench" else (0, 0)
+    R.sort_tensors(kt, vals, block_size=bs, num_chunks=pc)
     R.radsort_device_status()
     check_sorted_stable_perm(keys, kt, vals, 32)
     # sampled outputs the oracle computes one by one: rank of sampled keys
@@ -186,3 +193,33 @@ def test_full_size_2p28_properties(dist):
         pos = int((vals == idx).nonzero()[0, 0])
         k = host[idx]
         assert pos == int((host < k).sum()) + int((host[:idx] == k).sum())
+
+
+def test_full_size_float_2p28_bench_plan():
+    """float32 N(0,1) keys at 2^28 through the order-preserving transform."""
+    n = 1 << 28
+    host = W.make_keys("float", n)
+    keys = torch.from_numpy(host.view(np.int32)).to(DEV)
+    vals = torch.arange(n, dtype=torch.int32, device=DEV)
+    kt = keys.clone()
+    bs, pc = bench_plan()
+    R.sort_tensors(kt, vals, float_keys=True, block_size=bs, num_chunks=pc)
+    R.radsort_device_status()
+    f = kt.view(torch.float32)
+    assert bool((f[1:] >= f[:-1]).all())
+    v = vals.to(torch.int64) & 0xFFFFFFFF
+    assert torch.equal(keys[v], kt)
+    assert torch.equal(torch.sort(v).values, torch.arange(n, device=DEV))
+
+
+@pytest.mark.parametrize("db", [8, 11])
+def test_full_size_2p30_u64_properties(db):
+    """n = 2^30 uint64 keys uniform 64-bit + uint32 payloads (8-bit digits:
+    n_t = 8; 11-bit digits: n_t = 6), automatic plan."""
+    n = 1 << 30
+    r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=DEV)
+    kt = r.clone()
+    vals = torch.arange(n, dtype=torch.int32, device=DEV)
+    R.sort_tensors(kt, vals, digit_bits=db)
+    R.radsort_device_status()
+    check_sorted_stable_perm(r, kt, vals, 64)
