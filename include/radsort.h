@@ -122,6 +122,30 @@ radsort_status radsort_lsd_oop_sort(void *keys, uint32_t *values, void *keys_alt
                                     void *stream);
 
 /*
+ * Batched segmented sort: each segment [offsets[s], offsets[s+1]) of keys (and
+ * values) is sorted stably and independently (n = offsets[num_segments]).
+ * offsets_dev is the device copy of the num_segments+1 offsets (read by the
+ * kernels); offsets_host the same values on the host (used to plan the long
+ * segments).  Segments up to 4096 elements (2048 for 11-bit digits) are sorted
+ * in shared memory.  Segments up to 2^18 elements are sorted out of place in
+ * per-CTA scratch, the paper's suggestion of reusing T as the A' of Alg. 1 for
+ * short arrays (Sec. 5).  Both classes are handled by one persistent launch
+ * each.  Longer segments run the full Radsort (Alg. 2), or Alg. 1 with
+ * alternate buffers in the workspace when their start is not 16-byte aligned.
+ * workspace: at least radsort_segmented_workspace_size() bytes, or NULL to
+ * allocate stream-ordered.  With a caller workspace the call issues only
+ * kernel launches and memsets on `stream`, so it can be captured in a CUDA
+ * graph.
+ */
+radsort_status radsort_segmented_workspace_size(const uint64_t *offsets_host, size_t num_segments,
+                                                int key_bytes, int value_bytes, int digit_bits,
+                                                size_t *bytes);
+radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64_t *offsets_dev,
+                                      const uint64_t *offsets_host, size_t num_segments,
+                                      int key_bytes, int digit_bits, void *workspace,
+                                      size_t workspace_bytes, void *stream);
+
+/*
  * radsort_sort_noalloc: radsort_sort without any device allocation.  The
  * paper has no counterpart; this entry point exists for callers that cannot
  * allocate device memory at the point of the call -- code running inside a

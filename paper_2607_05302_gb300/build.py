@@ -29,7 +29,7 @@ def nvcc() -> str:
 
 
 def _flags(verbose_ptxas: bool):
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                 "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if verbose_ptxas:
         f += ["-Xptxas", "-v"]

@@ -417,6 +417,142 @@ radsort_status radsort_sort(void *keys, uint32_t *values, size_t n, int key_byte
 
 } // extern "C"
 
+// ---------------------------------------------------------------- segmented
+namespace {
+// plan of one large segment: block size 256, one chunk per 64K elements, at
+// most one per SM
+radsort_plan large_plan(size_t len)
+{
+    radsort_plan pl{};
+    pl.block_size = 256;
+    size_t p = len / 65536;
+    if (p < 1)
+        p = 1;
+    if (p > size_t(num_sms()))
+        p = num_sms();
+    pl.num_chunks = static_cast<uint32_t>(p);
+    return pl;
+}
+
+bool seg_aligned(size_t off, int kb, bool hasv)
+{
+    // keys and values start 16-byte aligned (the arrays themselves are)
+    return (off * kb) % 16 == 0 && (!hasv || (off * 4) % 16 == 0);
+}
+
+struct SegPlan {
+    size_t base = 0, large = 0, total = 0;
+};
+
+radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, SegPlan *sp)
+{
+    sp->base = (seg_scratch_bytes(kb, hasv, nseg) + 255) / 256 * 256;
+    size_t large = 0;
+    for (size_t s = 0; s < nseg; ++s) {
+        if (offh[s + 1] < offh[s])
+            return RADSORT_EINVAL;
+        const size_t len = offh[s + 1] - offh[s];
+        if (len <= SEG_MED)
+            continue;
+        size_t need;
+        if (seg_aligned(offh[s], kb, hasv)) {
+            const radsort_plan pl = large_plan(len);
+            Geom g;
+            if (fill_geom(len, kb, hasv, db, pl.block_size, pl.num_chunks, &g) != RADSORT_OK)
+                return RADSORT_EINVAL;
+            need = layout(g, nullptr, nullptr);
+        } else { // out of place, Alg. 1, with alternate buffers in the workspace
+            need = (len * kb + 255) / 256 * 256 + (hasv ? (len * 4 + 255) / 256 * 256 : 0) +
+                   lsd_oop_scratch_bytes(len, kb, db, hasv) + 256;
+        }
+        if (need > large)
+            large = need;
+    }
+    sp->large = large;
+    sp->total = sp->base + large;
+    return RADSORT_OK;
+}
+} // namespace
+
+extern "C" {
+
+radsort_status radsort_segmented_workspace_size(const uint64_t *offsets_host, size_t num_segments,
+                                                int key_bytes, int value_bytes, int digit_bits,
+                                                size_t *bytes)
+{
+    if (!bytes || (key_bytes != 4 && key_bytes != 8) || (value_bytes != 0 && value_bytes != 4) ||
+        (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
+        return RADSORT_EINVAL;
+    SegPlan sp;
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, &sp);
+    *bytes = s == RADSORT_OK ? sp.total : 0;
+    return s;
+}
+
+radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64_t *offsets_dev,
+                                      const uint64_t *offsets_host, size_t num_segments,
+                                      int key_bytes, int digit_bits, void *workspace,
+                                      size_t workspace_bytes, void *stream)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (num_segments == 0)
+        return RADSORT_OK;
+    if (!keys || !offsets_dev || !offsets_host || !aligned16(keys) || (values && !aligned16(values)))
+        return RADSORT_EINVAL;
+    if (num_segments >= (size_t(1) << 31))
+        return RADSORT_EINVAL;
+    const bool hasv = values != nullptr;
+    SegPlan sp;
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, &sp);
+    if (s != RADSORT_OK)
+        return s;
+    cudaStream_t st = as_stream(stream);
+    void *ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (workspace_bytes < sp.total)
+            return RADSORT_ENOMEM;
+        if (!aligned16(ws))
+            return RADSORT_EINVAL;
+    } else {
+        cudaError_t e = cudaMallocAsync(&ws, sp.total, st);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        own = true;
+    }
+    cudaError_t e = launch_segmented(keys, values, reinterpret_cast<const unsigned long long *>(offsets_dev),
+                                     num_segments, key_bytes, digit_bits, ws, st);
+    radsort_status rs = cuda_status(e);
+    char *lw = static_cast<char *>(ws) + sp.base;
+    for (size_t sg = 0; sg < num_segments && rs == RADSORT_OK; ++sg) {
+        const size_t off = offsets_host[sg], len = offsets_host[sg + 1] - off;
+        if (len <= SEG_MED)
+            continue;
+        char *sk = static_cast<char *>(keys) + off * key_bytes;
+        uint32_t *sv = hasv ? values + off : nullptr;
+        if (seg_aligned(off, key_bytes, hasv)) {
+            const radsort_plan pl = large_plan(len);
+            rs = sort_common(sk, sv, len, key_bytes, digit_bits, 0, &pl, lw, sp.large, stream, -1,
+                             nullptr, nullptr);
+        } else {
+            char *ak = lw;
+            char *av = ak + (len * key_bytes + 255) / 256 * 256;
+            char *sc = av + (hasv ? (len * 4 + 255) / 256 * 256 : 0);
+            rs = cuda_status(launch_lsd_oop_ws(sk, sv, ak, hasv ? reinterpret_cast<uint32_t *>(av) : nullptr,
+                                               len, key_bytes, digit_bits, sc, st));
+        }
+    }
+    if (own) {
+        cudaError_t e2 = cudaFreeAsync(ws, st);
+        if (rs == RADSORT_OK)
+            rs = cuda_status(e2);
+    }
+    return rs;
+}
+
+} // extern "C"
+
 // ---------------------------------------------------------------- no allocation
 // Scratch of radsort_sort_noalloc: one array in this library's device image.
 // Every GPU that loads the library holds these bytes until the process
@@ -532,7 +668,7 @@ radsort_status radsort_device_status(void *stream)
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess)
         return cuda_status(e);
-    const unsigned v = take_status_round() | take_status_finalize() | take_status_oop();
+    const unsigned v = take_status_round() | take_status_finalize() | take_status_oop() | take_status_seg();
     if (v & ST_TIMEOUT)
         return RADSORT_ETIMEOUT;
     if (v & ST_INTERNAL)

@@ -75,6 +75,18 @@ cudaError_t launch_float_keys(uint32_t *keys, size_t n, int inverse, cudaStream_
 cudaError_t launch_lsd_oop(void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
                            size_t n, int kb, int db, cudaStream_t st);
 
+// out-of-place LSD with caller scratch (nullptr: allocate stream-ordered)
+cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
+                              size_t n, int kb, int db, void *scratch, cudaStream_t st);
+size_t lsd_oop_scratch_bytes(size_t n, int kb, int db, bool hasv);
+// batched segmented sort of the small and medium segments
+constexpr uint32_t SEG_MED = 1u << 18;
+uint32_t seg_small_max(int db);
+size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg);
+cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long long *off_dev,
+                             size_t nseg, int kb, int db, void *scratch, cudaStream_t st);
+unsigned take_status_seg();
+
 int num_sms();
 // kernels launched by this library (host counter)
 extern std::atomic<unsigned long long> g_launches;

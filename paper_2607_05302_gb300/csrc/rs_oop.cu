@@ -231,8 +231,17 @@ __global__ void __launch_bounds__(NW * 32, 1)
 }
 
 template <typename KT, bool HASV, int DB, int TILE, int NW>
+static size_t oop_scratch(size_t n)
+{
+    constexpr int SIGMA = 1 << DB;
+    const int nt = (8 * int(sizeof(KT)) + DB - 1) / DB;
+    const size_t ntiles = (n + TILE - 1) / TILE;
+    return 2 * size_t(nt) * SIGMA * 8 + ntiles * SIGMA * 4 + 256;
+}
+
+template <typename KT, bool HASV, int DB, int TILE, int NW>
 static cudaError_t oop_impl(KT *keys, uint32_t *vals, KT *keys_alt, uint32_t *vals_alt, size_t n,
-                            cudaStream_t st)
+                            void *scratch, cudaStream_t st)
 {
     using C = OopCfg<KT, HASV, DB, TILE, NW>;
     constexpr int SIGMA = 1 << DB;
@@ -243,8 +252,11 @@ static cudaError_t oop_impl(KT *keys, uint32_t *vals, KT *keys_alt, uint32_t *va
     // scratch: histograms, offsets, look-back status, tickets
     const size_t hbytes = size_t(nt) * SIGMA * 8;
     const size_t sbytes = ntiles * SIGMA * 4;
-    char *scr = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scr), 2 * hbytes + sbytes + 256, st);
+    char *scr = static_cast<char *>(scratch);
+    const bool own = scr == nullptr;
+    cudaError_t e = cudaSuccess;
+    if (own)
+        e = cudaMallocAsync(reinterpret_cast<void **>(&scr), oop_scratch<KT, HASV, DB, TILE, NW>(n), st);
     if (e != cudaSuccess)
         return e;
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(scr);
@@ -289,28 +301,51 @@ static cudaError_t oop_impl(KT *keys, uint32_t *vals, KT *keys_alt, uint32_t *va
             cudaMemcpyAsync(vals, vs, n * 4, cudaMemcpyDeviceToDevice, st);
     }
     e = cudaGetLastError();
-    cudaError_t e2 = cudaFreeAsync(scr, st);
+    cudaError_t e2 = own ? cudaFreeAsync(scr, st) : cudaSuccess;
     return e != cudaSuccess ? e : e2;
+}
+
+// Calls f.template operator()<KT, HASV, DB, TILE, NW>() for the configuration.
+template <typename F> static cudaError_t oop_dispatch(int kb, int db, bool hasv, F &&f)
+{
+    using u64 = unsigned long long;
+    if (kb == 4) {
+        if (db == 8)
+            return hasv ? f.template operator()<uint32_t, true, 8, 4096, 16>()
+                        : f.template operator()<uint32_t, false, 8, 4096, 16>();
+        return hasv ? f.template operator()<uint32_t, true, 11, 4096, 8>()
+                    : f.template operator()<uint32_t, false, 11, 4096, 8>();
+    }
+    if (db == 8)
+        return hasv ? f.template operator()<u64, true, 8, 4096, 16>()
+                    : f.template operator()<u64, false, 8, 4096, 16>();
+    return hasv ? f.template operator()<u64, true, 11, 4096, 8>()
+                : f.template operator()<u64, false, 11, 4096, 8>();
+}
+
+size_t lsd_oop_scratch_bytes(size_t n, int kb, int db, bool hasv)
+{
+    size_t r = 0;
+    oop_dispatch(kb, db, hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW>() {
+        r = oop_scratch<KT, HASV, DB, TILE, NW>(n);
+        return cudaSuccess;
+    });
+    return r;
+}
+
+cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
+                              size_t n, int kb, int db, void *scratch, cudaStream_t st)
+{
+    return oop_dispatch(kb, db, vals != nullptr, [&]<typename KT, bool HASV, int DB, int TILE, int NW>() {
+        return oop_impl<KT, HASV, DB, TILE, NW>(static_cast<KT *>(keys), vals, static_cast<KT *>(keys_alt),
+                                                vals_alt, n, scratch, st);
+    });
 }
 
 cudaError_t launch_lsd_oop(void *keys, uint32_t *vals, void *keys_alt, uint32_t *vals_alt,
                            size_t n, int kb, int db, cudaStream_t st)
 {
-    using u64 = unsigned long long;
-    if (kb == 4) {
-        auto k = static_cast<uint32_t *>(keys), ka = static_cast<uint32_t *>(keys_alt);
-        if (db == 8)
-            return vals ? oop_impl<uint32_t, true, 8, 4096, 16>(k, vals, ka, vals_alt, n, st)
-                        : oop_impl<uint32_t, false, 8, 4096, 16>(k, vals, ka, vals_alt, n, st);
-        return vals ? oop_impl<uint32_t, true, 11, 4096, 8>(k, vals, ka, vals_alt, n, st)
-                    : oop_impl<uint32_t, false, 11, 4096, 8>(k, vals, ka, vals_alt, n, st);
-    }
-    auto k = static_cast<u64 *>(keys), ka = static_cast<u64 *>(keys_alt);
-    if (db == 8)
-        return vals ? oop_impl<u64, true, 8, 4096, 16>(k, vals, ka, vals_alt, n, st)
-                    : oop_impl<u64, false, 8, 4096, 16>(k, vals, ka, vals_alt, n, st);
-    return vals ? oop_impl<u64, true, 11, 4096, 8>(k, vals, ka, vals_alt, n, st)
-                : oop_impl<u64, false, 11, 4096, 8>(k, vals, ka, vals_alt, n, st);
+    return launch_lsd_oop_ws(keys, vals, keys_alt, vals_alt, n, kb, db, nullptr, st);
 }
 
 } // namespace rs

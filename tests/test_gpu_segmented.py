@@ -1,0 +1,129 @@
+"""GPU parity of the batched segmented sort (many independent arrays in one
+call) against the oracle, and the 20,000-segment lognormal workload at full
+size by properties that fix a stable sort."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2607_05302_gb300 import radsort as R
+from paper_2607_05302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def offsets_of(lengths):
+    off = np.zeros(len(lengths) + 1, dtype=np.uint64)
+    np.cumsum(np.asarray(lengths, dtype=np.uint64), out=off[1:])
+    return off
+
+
+def run_segmented(keys_np, lengths, digit_bits=8, caller_ws=True):
+    off = offsets_of(lengths)
+    n = int(off[-1])
+    kt = torch.from_numpy(keys_np.view(np.int32 if keys_np.dtype == np.uint32 else np.int64)).to(DEV)
+    vt = torch.arange(n, dtype=torch.int32, device=DEV)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    ws = None
+    if caller_ws:
+        need = R.segmented_workspace_size(off, keys_np.itemsize, 4, digit_bits)
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=DEV)
+    R.sort_segmented_tensors(kt, vt, od, off, digit_bits=digit_bits, workspace=ws)
+    R.radsort_device_status()
+    return kt, vt, off
+
+
+def oracle_segmented_u32(keys, lengths, digit_bits=8):
+    """The oracle's stable LSD sort on the composite key (segment << 32 | key):
+    per-segment stable sort, in one oracle call."""
+    seg = np.repeat(np.arange(len(lengths), dtype=np.uint64), lengths)
+    comp = (seg << np.uint64(32)) | keys.astype(np.uint64)
+    nbits = 32 + max(1, int(len(lengths) - 1).bit_length())
+    n_t = oracle.digits_for(nbits, digit_bits)
+    k, v = oracle.lsd_oop(comp, np.arange(keys.size, dtype=np.uint32), n_t=n_t, sigma=1 << digit_bits,
+                          bits=digit_bits)
+    return (k & np.uint64(0xFFFFFFFF)).astype(np.uint32), v
+
+
+LENGTH_SETS = {
+    # every class: tiny, small (<= 4096), medium (<= 2^18), large aligned and misaligned
+    "mixed": [1, 0, 2, 17, 4095, 4096, 4097, 70000, 1 << 18, (1 << 18) + 1, 300001, 3, 5000,
+              (1 << 18) + 4, 12345],
+    "many_small": list(W.lognormal_lengths(3000, median=300.0, sigma_ln=1.5, lo=0, hi=5000)),
+}
+
+
+@pytest.mark.parametrize("lengths", list(LENGTH_SETS), ids=list(LENGTH_SETS))
+@pytest.mark.parametrize("digit_bits", [8, 11])
+def test_segmented_u32_vs_oracle(lengths, digit_bits):
+    lens = [int(x) for x in LENGTH_SETS[lengths]]
+    n = sum(lens)
+    rng = np.random.default_rng(len(lens) + digit_bits)
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    keys[::5] = keys[0]  # ties across and within segments
+    kt, vt, _ = run_segmented(keys, lens, digit_bits)
+    ek, ev = oracle_segmented_u32(keys, lens, digit_bits)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
+@pytest.mark.parametrize("digit_bits", [8, 11])
+def test_segmented_u64_vs_oracle(digit_bits):
+    lens = [5, 4096, 2049, 300000, 77777, 1 << 18, (1 << 18) + 2, 1]
+    n = sum(lens)
+    keys = W.make_keys("uniform", n, 64)
+    keys[::3] = keys[1]
+    kt, vt, off = run_segmented(keys, lens, digit_bits)
+    gk = kt.cpu().numpy().view(np.uint64)
+    gv = vt.cpu().numpy().view(np.uint32)
+    n_t = oracle.digits_for(64, digit_bits)
+    for s in range(len(lens)):
+        a, b = int(off[s]), int(off[s + 1])
+        ek, ev = oracle.lsd_oop(keys[a:b], np.arange(a, b, dtype=np.uint32), n_t=n_t,
+                                sigma=1 << digit_bits, bits=digit_bits)
+        assert np.array_equal(gk[a:b], ek) and np.array_equal(gv[a:b], ev), s
+
+
+def test_segmented_keys_only_and_internal_workspace():
+    lens = [100, 5000, 300000, 1, 0, 9999]
+    n = sum(lens)
+    keys = W.make_keys("uniform", n)
+    off = offsets_of(lens)
+    kt = torch.from_numpy(keys.view(np.int32)).to(DEV)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    R.sort_segmented_tensors(kt, None, od, off)
+    R.radsort_device_status()
+    got = kt.cpu().numpy().view(np.uint32)
+    for s in range(len(lens)):
+        a, b = int(off[s]), int(off[s + 1])
+        assert np.array_equal(got[a:b], np.sort(keys[a:b]))
+
+
+def test_config4_20000_lognormal_segments_properties():
+    """20,000 uint32 arrays, lengths lognormal (median 4096, natural-log sigma
+    2, clipped to [16, 2^22]), index payloads, one call."""
+    lens = W.lognormal_lengths(20000)
+    off = offsets_of(lens)
+    n = int(off[-1])
+    r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=DEV)
+    keys0 = ((r >> 32) & 0xFFFFFFFF).to(torch.int64)
+    del r
+    kt = keys0.to(torch.int32)
+    vt = torch.arange(n, dtype=torch.int32, device=DEV)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    need = R.segmented_workspace_size(off, 4, 4)
+    ws = torch.empty(need, dtype=torch.uint8, device=DEV)
+    R.sort_segmented_tensors(kt, vt, od, off, workspace=ws)
+    R.radsort_device_status()
+    seg = torch.repeat_interleave(torch.arange(len(lens), device=DEV),
+                                  torch.from_numpy(lens.astype(np.int64)).to(DEV))
+    v = vt.to(torch.int64) & 0xFFFFFFFF
+    k = kt.to(torch.int64) & 0xFFFFFFFF
+    assert torch.equal(torch.sort(v).values, torch.arange(n, device=DEV))  # a permutation
+    assert torch.equal(seg[v], seg)  # that stays inside each segment
+    assert torch.equal(keys0[v], k)  # carrying each key with its payload
+    same = seg[1:] == seg[:-1]
+    assert bool((k[1:][same] >= k[:-1][same]).all())  # sorted per segment
+    eq = same & (k[1:] == k[:-1])
+    assert bool((v[1:][eq] > v[:-1][eq]).all())  # stable
