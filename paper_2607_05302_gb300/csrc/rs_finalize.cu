@@ -810,7 +810,9 @@ FinLayout fin_layout(const Geom &g)
     L.nstr = g.npi / K + 2;
     L.nwin = static_cast<uint32_t>(g.n / L.W + 2);
     L.nrec = L.nstr + 1;
-    L.nslots = 1024;
+    // slots for cycles that span strides: a handful in practice; the rest are
+    // moved by one CTA each, so small sorts keep a small workspace
+    L.nslots = g.npi / 64 < 16 ? 16 : (g.npi / 64 > 1024 ? 1024 : g.npi / 64);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     L.ctr = off;
