@@ -121,6 +121,8 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES> struct R
     static constexpr int ITEMS = R / 32;     // elements per consumer thread
     static_assert(R % 32 == 0, "warp range must be a multiple of 32");
     static_assert(THREADS <= 1024, "one CTA holds at most 1024 threads");
+    // CTAs per SM the configuration is built for (registers are capped accordingly)
+    static constexpr int MINB = (NW <= 8 && DB <= 8) ? 2 : 1;
     // column scan over the warps' counts: TPB adjacent lanes per bucket
     static constexpr int TPB = NW >= 16 ? 4 : (NW >= 4 ? 2 : 1);
     static_assert(NW % TPB == 0, "rows split evenly");
@@ -229,7 +231,8 @@ scan2(uint32_t *a, uint32_t *bb, uint32_t *tmp, uint32_t &tot_a, uint32_t &tot_b
 }
 
 template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES>
-__global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THREADS, 1)
+__global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THREADS,
+                                   RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::MINB)
     k_round(RoundArgs<KT> a)
 {
     using C = RoundCfg<KT, HASV, DB, TILE, NW, STAGES>;
@@ -678,9 +681,14 @@ cudaError_t launch_round(const Geom &g, const Bufs &w, const uint32_t *pi, const
     using u64 = unsigned long long;
     //                       key  vals  d   TILE  NW  STAGES
     if (g.kb == 4) {
-        if (g.db == 8)
+        if (g.db == 8) {
+            // more chunks than SMs: two smaller CTAs per SM hide each other's barriers
+            if (g.p > static_cast<uint32_t>(num_sms()))
+                return g.hasv ? round_impl<uint32_t, true, 8, 4096, 8, 2>(g, w, pi, lo, UC, round, st)
+                              : round_impl<uint32_t, false, 8, 4096, 8, 3>(g, w, pi, lo, UC, round, st);
             return g.hasv ? round_impl<uint32_t, true, 8, 8192, 16, 2>(g, w, pi, lo, UC, round, st)
                           : round_impl<uint32_t, false, 8, 8192, 16, 3>(g, w, pi, lo, UC, round, st);
+        }
         return g.hasv ? round_impl<uint32_t, true, 11, 4096, 8, 2>(g, w, pi, lo, UC, round, st)
                       : round_impl<uint32_t, false, 11, 4096, 8, 3>(g, w, pi, lo, UC, round, st);
     }

@@ -39,7 +39,7 @@ def oracle_sort(keys, vals, key_bits, digit_bits):
 
 
 SIZES = [2, 3, 63, 64, 65, 255, 256, 257, 4095, 4096, 4097, 10000, 65543, 300001]
-PLANS = [(64, 1), (64, 3), (256, 2), (1024, 4), (4096, 1), (0, 0)]
+PLANS = [(64, 1), (64, 3), (256, 2), (1024, 4), (4096, 1), (0, 0), (256, 300)]
 
 
 @pytest.mark.parametrize("plan", PLANS)
