@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--num-chunks", type=int, default=0)
+    ap.add_argument("--layout", default="auto", choices=["auto", "grid", "chunks"],
+                    help="block layout (auto: the automatic plan, the grid layout below 2^31)")
     ap.add_argument("--no-oop", action="store_true", help="skip the out-of-place comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
@@ -192,6 +194,21 @@ def profiled_traffic(n, kb, db):
     if not m or not t or m.group(1) != round_kernel_hash() or kb != 4 or db != 8:
         return None
     return round(float(t.group(1)) * n)
+
+
+def oop_scratch_bytes(n, kb, db):
+    """Scratch of the out-of-place comparator besides its alternate arrays:
+    digit histograms and offsets, and the look-back ring (R tiles x sigma
+    64-bit words plus R done tags), as the library sizes them."""
+    sigma = 1 << db
+    nt = -(-8 * kb // db)
+    tile = {(4, 8): 8192, (4, 11): 4096, (8, 8): 4096, (8, 11): 2048}[(kb, db)]
+    ntiles = -(-n // tile)
+    rows = 1
+    while rows < ntiles and rows < (4096 if sigma <= 256 else 1024):
+        rows <<= 1
+    al = lambda x: (x + 255) // 256 * 256
+    return al(nt * sigma * 4) + al(nt * (sigma + 1) * 4) + al(rows * sigma * 8 + rows * 4) + al(256)
 
 
 def end_to_end(a, R, keys0, vals0, dk, dv, n, kb, db, E, world, barrier, stream):
@@ -354,12 +371,17 @@ def main():
     vals0 = torch.arange(n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
-    # throughput plan: one chunk per SM, b = 256 (the 2% memory plan is timed
-    # beside it, see plan_2pct)
+    # the automatic plan (grid layout, block size of least workspace); the
+    # chunk layout with one chunk per SM is timed beside it (chunk_layout)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    bs = a.block_size or 256
-    pc = a.num_chunks or sms
-    wsb = R.radsort_workspace_size(n, kb, 4, db, bs, pc)
+    lay = a.layout
+    if lay == "chunks":
+        bs, pc = a.block_size or 256, a.num_chunks or sms
+    else:
+        bs, pc = a.block_size, 0
+    wsb = R.radsort_workspace_size(n, kb, 4, db, bs, pc, lay)
+    if not bs:
+        bs, _, _ = R.radsort_plan_default(n, kb, 4, db)
     ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
 
     free_b = torch.cuda.mem_get_info(dev)[0]
@@ -377,7 +399,7 @@ def main():
 
     def step(i):
         R.sort_tensors(kbufs[i % nbuf], vbufs[i % nbuf], digit_bits=db, block_size=bs,
-                       num_chunks=pc, workspace=ws)
+                       num_chunks=pc, workspace=ws, layout=lay)
 
     # warm-up (also checks the result once against the sorted reference)
     for i in range(a.warmup):
@@ -429,30 +451,32 @@ def main():
     traffic = profiled_traffic(n, kb, db)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "kernel": "k_round (sortPhase, Alg. 5)",
+                "kernel": ("k_round (sortPhase, Alg. 5, chunk layout)" if lay == "chunks"
+                           else "k_lb_round (sortPhase, Alg. 5, grid layout)"),
                 "algorithmic_bytes_per_launch": n * 2 * E, "peak_source": src,
                 "avg_launch_ms": round(avg_round, 4)}
     step_bytes = n * (4 * 2 * E) if kb == 4 and db == 8 else None
 
-    # ---- the 2% memory plan (automatic plan) on the same data
+    # ---- the paper's chunk layout (Sec. 4.3), one chunk per SM, same data
     plan2 = None
-    if not a.no_oop:
-        b2, p2 = R.radsort_plan_default(n, kb, 4, db)
-        ws2 = R.radsort_workspace_size(n, kb, 4, db, b2, p2)
+    if not a.no_oop and lay != "chunks":
+        b2, p2 = 256, sms
+        ws2 = R.radsort_workspace_size(n, kb, 4, db, b2, p2, "chunks")
         wst = torch.empty(max(ws2, 1), dtype=torch.uint8, device=dev)
         for i in range(min(nbuf, 2)):
             refill(i)
-        R.sort_tensors(kbufs[0], vbufs[0], digit_bits=db, block_size=b2, num_chunks=p2, workspace=wst)
+        R.sort_tensors(kbufs[0], vbufs[0], digit_bits=db, block_size=b2, num_chunks=p2, workspace=wst,
+                       layout="chunks")
         barrier()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record(stream)
         R.sort_tensors(kbufs[1 % nbuf], vbufs[1 % nbuf], digit_bits=db, block_size=b2, num_chunks=p2,
-                       workspace=wst)
+                       workspace=wst, layout="chunks")
         q1.record(stream)
         barrier()
         R.radsort_device_status()
         pms = q0.elapsed_time(q1)
-        plan2 = {"block_size": b2, "num_chunks": p2, "extra_bytes": ws2,
+        plan2 = {"layout": "chunks", "block_size": b2, "num_chunks": p2, "extra_bytes": ws2,
                  "extra_frac": round(ws2 / (n * E), 5), "value": round(world * n / (pms / 1e3) / 1e9, 3),
                  "unit": "Gkeys/s", "ms_per_step": round(pms, 3), "steps": 1}
         del wst
@@ -488,7 +512,8 @@ def main():
         oms = o0.elapsed_time(o1)
         oval = world * a.steps * n / (oms / 1e3) / 1e9
         oop = {"value": round(oval, 3), "unit": "Gkeys/s", "ms_per_step": oms / a.steps,
-               "extra_bytes": n * E + (n // 4096 + 1) * (1 << db) * 4,
+               # the alternate arrays plus histograms and the look-back ring
+               "extra_bytes": n * E + oop_scratch_bytes(n, kb, db),
                "radsort_over_oop": round(value / oval, 4)}
         del ka, va
 
@@ -505,12 +530,13 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32" if kb == 4 else "u64", "data": "synthetic",
             "config": {"workload": workload_name(a), "n": n, "key_bytes": kb, "value_bytes": 4,
-                       "digit_bits": db, "block_size": bs, "num_chunks": pc,
+                       "digit_bits": db, "layout": "chunks" if lay == "chunks" else "grid",
+                       "block_size": bs, "num_chunks": pc,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2: each timed step sorts its own fresh 2^%d-element copy" % a.log2n},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
-            "oop": oop, "plan_2pct": plan2,
+            "oop": oop, "chunk_layout": plan2,
             "phases_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
             "algorithmic_bytes_per_step": step_bytes,
         }

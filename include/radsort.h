@@ -51,12 +51,31 @@ typedef enum {
                                     bit transform applied before and undone
                                     after the sort. */
 
-/* Tuning plan.  Zero fields mean "choose automatically". */
+/*
+ * Block layouts (radsort_plan.layout).
+ *  RADSORT_LAYOUT_CHUNKS: the paper's parallel variant (Sec. 4.3).  The array
+ *    is split into p chunks, each with its own head start of sigma blocks and
+ *    its own chain of blocks per bucket; T holds 2*sigma*p blocks.
+ *  RADSORT_LAYOUT_GRID: one free list and one chain per bucket for the whole
+ *    array, as in the sequential algorithm (Sec. 2), laid on the block grid of
+ *    each round's output (blocks that hold the start of a bucket are shared
+ *    by the buckets in them).  All SMs work on it through a decoupled
+ *    look-back; T holds 4*sigma + 1 blocks whatever the parallelism, and
+ *    after the last round every block but the tail is full.  Needs n < 2^31.
+ */
+#define RADSORT_LAYOUT_AUTO 0u
+#define RADSORT_LAYOUT_CHUNKS 1u
+#define RADSORT_LAYOUT_GRID 2u
+
+/* Tuning plan.  Zero fields mean "choose automatically" (the grid layout
+ * when n < 2^31, with the block size of least workspace). */
 typedef struct {
     uint32_t block_size; /* b: elements per block, power of two in [64, 4096] */
-    uint32_t num_chunks; /* p: chunks sorted in parallel, each with its own
-                            head start of sigma blocks (Sec. 4.3) */
-    uint32_t reserved[6];
+    uint32_t num_chunks; /* p (chunk layout): chunks sorted in parallel, each
+                            with its own head start of sigma blocks (Sec. 4.3);
+                            nonzero with layout AUTO selects the chunk layout */
+    uint32_t layout;     /* RADSORT_LAYOUT_* */
+    uint32_t reserved[5];
 } radsort_plan;
 
 /* Human-readable name of a status code (static storage). */
@@ -67,11 +86,13 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
                                     radsort_plan *plan);
 
 /*
- * Bytes of device workspace radsort_sort_ex needs: the scratch array T of
- * 2*sigma*p blocks (Sec. 2.1, Sec. 4.3), the block permutation pi and its
- * successor, the usage array U (Alg. 5-6), the partial-block list P and the
- * per-chunk counters.  This is the sort's whole extra device memory beyond
- * the caller's arrays.  value_bytes is 0 or 4.
+ * Bytes of device workspace radsort_sort_ex needs: the scratch array T
+ * (2*sigma*p blocks in the chunk layout, Sec. 2.1 and 4.3; 4*sigma + 1 in the
+ * grid layout), the block permutation pi and its successor, the usage array
+ * U (Alg. 5-6, chunk layout), the partial-block list P, the per-chunk
+ * counters or (grid layout) the digit histograms and the look-back words of
+ * one round.  This is the sort's whole extra device memory beyond the
+ * caller's arrays.  value_bytes is 0 or 4.
  */
 radsort_status radsort_workspace_size(size_t n, int key_bytes, int value_bytes, int digit_bits,
                                       const radsort_plan *plan, size_t *bytes);

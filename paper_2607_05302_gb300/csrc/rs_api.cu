@@ -128,6 +128,39 @@ static radsort_status fill_geom(size_t n, int kb, bool hasv, int db, uint32_t b,
     g->nT = static_cast<uint32_t>(2 * H);
     g->npi = static_cast<uint32_t>(npi);
     g->G = static_cast<uint32_t>(H);
+    g->grid = false;
+    return RADSORT_OK;
+}
+
+// Geometry of the grid layout (one chain per bucket on the output block
+// grid): head start (GRID_AHEAD + 2)*sigma, scratch H + 1 blocks (the last
+// holds the input tail), the data in logical blocks H .. H + nA.
+static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32_t b, Geom *g)
+{
+    if (!pow2(b) || b < 64 || b > 4096 || b > lb_tile(kb, db, hasv))
+        return RADSORT_EINVAL; // a tile holds whole blocks
+    if (n >= (size_t(1) << 31))
+        return RADSORT_EINVAL; // look-back words hold 31-bit prefixes
+    g->n = n;
+    g->kb = kb;
+    g->hasv = hasv;
+    g->db = db;
+    g->sigma = 1u << db;
+    g->nt = (8 * kb + db - 1) / db;
+    g->b = b;
+    g->lb = ilog2(b);
+    g->p = 1;
+    g->grid = true;
+    const unsigned long long nA = n / b;
+    const unsigned long long H = (GRID_AHEAD + 2ull) * g->sigma;
+    const unsigned long long npi = nA + H + 1;
+    if (npi >= (1ull << 28))
+        return RADSORT_EINVAL;
+    g->nA = static_cast<uint32_t>(nA);
+    g->H = static_cast<uint32_t>(H);
+    g->nT = static_cast<uint32_t>(H + 1);
+    g->npi = static_cast<uint32_t>(npi);
+    g->G = 1;
     return RADSORT_OK;
 }
 
@@ -135,7 +168,43 @@ static radsort_status fill_geom(size_t n, int kb, bool hasv, int db, uint32_t b,
 // trades chunk parallelism p against block size b.  It keeps the whole
 // workspace within 2% of the array's bytes (with a floor for small arrays),
 // uses at most one chunk per SM and at least ~64K elements per chunk.
+static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl);
+
+// Automatic plan: the grid layout (its extra memory does not grow with the
+// number of CTAs) with the block size of least workspace; the chunk layout
+// (Sec. 4.3) when n >= 2^31 or when the plan asks for it.
 static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
+{
+    const long el = env_long("RADSORT_LAYOUT", 0);
+    const uint32_t want = pl->layout ? pl->layout : static_cast<uint32_t>(el);
+    if (want != RADSORT_LAYOUT_CHUNKS && n < (size_t(1) << 31)) {
+        uint32_t best_b = 0;
+        size_t best = 0;
+        for (uint32_t b : {512u, 1024u, 256u, 2048u}) {
+            Geom g;
+            if (fill_geom_grid(n, kb, vb != 0, db, b, &g) != RADSORT_OK)
+                continue;
+            const size_t sz = layout(g, nullptr, nullptr);
+            if (!best_b || sz < best) {
+                best = sz;
+                best_b = b;
+            }
+        }
+        if (best_b) {
+            pl->layout = RADSORT_LAYOUT_GRID;
+            pl->block_size = best_b;
+            pl->num_chunks = 1;
+            const long eb = env_long("RADSORT_B", 0);
+            if (eb > 0)
+                pl->block_size = static_cast<uint32_t>(eb);
+            return;
+        }
+    }
+    pl->layout = RADSORT_LAYOUT_CHUNKS;
+    auto_plan_chunks(n, kb, vb, db, pl);
+}
+
+static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl)
 {
     const size_t E = kb + vb;
     double budget = 0.02 * double(n) * double(E);
@@ -193,11 +262,20 @@ static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radso
 {
     if ((kb != 4 && kb != 8) || (db != 8 && db != 11))
         return RADSORT_EINVAL;
+    if (plan && plan->layout > RADSORT_LAYOUT_GRID)
+        return RADSORT_EINVAL;
     radsort_plan pl{};
-    if (!plan || !plan->block_size || !plan->num_chunks)
+    if (plan)
+        pl.layout = plan->layout;
+    // a chunk count without a layout means the chunk layout
+    if (plan && plan->num_chunks && !plan->layout)
+        pl.layout = RADSORT_LAYOUT_CHUNKS;
+    if (!plan || !plan->block_size || (pl.layout != RADSORT_LAYOUT_GRID && !plan->num_chunks))
         auto_plan(n, kb, hasv ? 4 : 0, db, &pl);
     if (plan && plan->block_size)
         pl.block_size = plan->block_size;
+    if (pl.layout == RADSORT_LAYOUT_GRID)
+        return fill_geom_grid(n, kb, hasv, db, pl.block_size, g);
     if (plan && plan->num_chunks)
         pl.num_chunks = plan->num_chunks;
     return fill_geom(n, kb, hasv, db, pl.block_size, pl.num_chunks, g);
@@ -216,6 +294,29 @@ static size_t layout(const Geom &g, void *base, Bufs *w)
     const size_t tel = size_t(g.nT) * g.b;
     const size_t npi2 = g.npi + (g.npi & 1);
     Bufs b{};
+    if (g.grid) {
+        // [T keys | T values | piX | piY | tables | state | Z], Z = the
+        // look-back words during the rounds, then Finalize's jump array and
+        // scratch
+        b.Tk = take(tel * g.kb);
+        b.Tv = static_cast<uint32_t *>(g.hasv ? take(tel * 4) : nullptr);
+        b.aux = static_cast<uint32_t *>(take(2 * npi2 * 4));
+        b.P = static_cast<uint2 *>(take(8));
+        b.E = static_cast<unsigned long long *>(take(2 * 8));
+        b.state = static_cast<uint32_t *>(take(ST_WORDS * 4));
+        b.ctr = static_cast<uint32_t *>(take(64 * 4));
+        b.hist = static_cast<uint32_t *>(take(size_t(g.nt) * g.sigma * 4));
+        b.tab = static_cast<uint32_t *>(take((4 * size_t(g.sigma) + 4) * 4));
+        const size_t jump = align_up(npi2 * 8, 256), fin = finalize_extra_bytes(g);
+        const size_t lbw = grid_ring_bytes(g);
+        char *z = static_cast<char *>(take(lbw > jump + fin ? lbw : jump + fin));
+        b.status = reinterpret_cast<uint32_t *>(z);
+        b.fin = base ? z + jump : nullptr;
+        off = align_up(off, 256);
+        if (w)
+            *w = b;
+        return off;
+    }
     b.Tk = take(tel * g.kb);
     b.Tv = static_cast<uint32_t *>(g.hasv ? take(tel * 4) : nullptr);
     b.aux = static_cast<uint32_t *>(take(3 * npi2 * 4));
@@ -254,9 +355,36 @@ static cudaError_t run_rounds(const Geom &g, Bufs &w, int rounds, cudaStream_t s
                               uint32_t **pi_cur, uint32_t **pi_oth)
 {
     const size_t npi2 = g.npi + (g.npi & 1);
+    cudaError_t e;
+    if (g.grid) {
+        uint32_t *pc = w.aux, *pn = w.aux + npi2;
+        e = cudaMemsetAsync(w.state, 0, ST_WORDS * 4, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(w.ctr, 0, 64 * 4, st);
+        if (e == cudaSuccess) {
+            Scope sc(0, -1, st);
+            e = launch_grid_setup(g, w, pc, st);
+        }
+        for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+            {   // the tables of this digit and the parts of the next map
+                // known before the round (head start, shared blocks)
+                Scope sc(2, r, st);
+                e = launch_grid_prep(g, w, pc, pn, r, st);
+            }
+            if (e == cudaSuccess) {
+                Scope sc(1, r, st);
+                e = launch_grid_round(g, w, pc, pn, r, st);
+            }
+            uint32_t *t = pc;
+            pc = pn;
+            pn = t;
+        }
+        *pi_cur = pc;
+        *pi_oth = pn;
+        return e;
+    }
     uint32_t *piX = w.aux, *UC = w.aux + npi2, *piY = w.aux + 2 * npi2;
     uint32_t *pc = piX, *pn = piY, *lc = w.lo0, *ln = w.lo1;
-    cudaError_t e;
     {
         Scope sc(0, -1, st);
         e = launch_setup(g, w, pc, st);
@@ -381,8 +509,9 @@ static radsort_status sort_common(void *keys, uint32_t *values, size_t n, int ke
         if (rounds < 0) {
             Scope sc(3, -1, st);
             // 2*npi words of scratch: U and the idle pi buffer, adjacent
+            // (grid layout: the look-back words, no longer needed)
             const size_t npi2 = g.npi + (g.npi & 1);
-            uint32_t *jw = pc == w.aux ? w.aux + npi2 : w.aux;
+            uint32_t *jw = g.grid ? w.status : (pc == w.aux ? w.aux + npi2 : w.aux);
             e = launch_finalize(g, w, pc, reinterpret_cast<unsigned long long *>(jw), st);
             (void)po;
         } else

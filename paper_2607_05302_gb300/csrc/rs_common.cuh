@@ -29,6 +29,13 @@ __device__ __forceinline__ void set_status(unsigned bits) { atomicOr(&g_status, 
 // limit is several seconds of wall time on a healthy GPU).
 constexpr unsigned SPIN_LIMIT = 1u << 26;
 
+// True once any wait of this translation unit has run out: the other waits
+// give up at their next check instead of running out one after another.
+__device__ __forceinline__ bool wait_failed()
+{
+    return (*reinterpret_cast<volatile unsigned *>(&g_status) & ST_TIMEOUT) != 0;
+}
+
 // ---------------------------------------------------------------- smem / mbarrier / bulk copy
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -77,6 +84,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
         if (mbar_try_wait(bar, parity))
             return true;
+        if ((it & 1023u) == 1023u && wait_failed())
+            return false;
         __nanosleep(64);
     }
     set_status(ST_TIMEOUT);

@@ -130,6 +130,8 @@ __device__ __forceinline__ bool wait_flag(const uint32_t *p)
     for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
         if (ld_acquire(p))
             return true;
+        if ((it & 1023u) == 1023u && wait_failed())
+            return false;
         __nanosleep(64);
     }
     set_status(ST_TIMEOUT);
@@ -791,6 +793,18 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
     }
 }
 
+// grid layout: the tail block (logical nA) was moved to scratch block 0
+template <typename KT> __global__ void k_fz_tail(FinArgs a, uint32_t tail)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= tail)
+        return;
+    const size_t dst = size_t(a.nA) * a.b + j;
+    static_cast<KT *>(a.Ak)[dst] = kblk<KT>(a, 0)[j];
+    if (a.Av)
+        a.Av[dst] = vblk(a, 0)[j];
+}
+
 struct FinLayout {
     size_t ctr, sflag, wflag, slotflag, rec, wplan, wsegs, slotk, slotv, total;
     uint32_t K, W, nstr, nwin, nrec, nslots;
@@ -808,7 +822,7 @@ FinLayout fin_layout(const Geom &g)
     L.K = K;
     L.W = g.kb == 4 ? 8192 : 4096;
     L.nstr = g.npi / K + 2;
-    L.nwin = static_cast<uint32_t>(g.n / L.W + 2);
+    L.nwin = g.grid ? 0u : static_cast<uint32_t>(g.n / L.W + 2); // windows of F2 (chunk layout only)
     L.nrec = L.nstr + 1;
     // slots for cycles that span strides: a handful in practice; the rest are
     // moved by one CTA each, so small sorts keep a small workspace
@@ -874,9 +888,11 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     cudaError_t e = cudaMemsetAsync(base, 0, L.rec, st);
     if (e != cudaSuccess)
         return e;
-    e = launch_deficit(g, w, st); // D over the last round's P, used by F2
-    if (e != cudaSuccess)
-        return e;
+    if (!g.grid) {
+        e = launch_deficit(g, w, st); // D over the last round's P, used by F2
+        if (e != cudaSuccess)
+            return e;
+    }
     const int sms = num_sms();
     int grid = static_cast<int>((g.npi + FIN_T - 1) / FIN_T);
     if (grid > sms * 8)
@@ -916,6 +932,15 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_move<KT>, FIN_T, msm);
     k_fz_move<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, msm, st>>>(a);
     k_fz_move_deferred<KT><<<sms, FIN_T, msm, st>>>(a);
+    if (g.grid) {
+        // every block but the last is full: only the tail (now in scratch
+        // block 0) remains to be copied behind A's last block
+        const uint32_t tail = static_cast<uint32_t>(g.n - size_t(g.nA) * g.b);
+        if (tail)
+            k_fz_tail<KT><<<(tail + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, tail);
+        g_launches += 10 + 2 * rounds;
+        return cudaGetLastError();
+    }
     uint4 *wplan = reinterpret_cast<uint4 *>(base + L.wplan);
     uint4 *wsegs = reinterpret_cast<uint4 *>(base + L.wsegs);
     k_fz_winplan<<<(L.nwin + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, wplan, wsegs);

@@ -24,8 +24,9 @@ struct Geom {
     uint32_t nA;       // floor(n/b): blocks overlaying A
     uint32_t H;        // head start sigma*p
     uint32_t nT;       // scratch blocks 2H
-    uint32_t npi;      // nA + 2H
+    uint32_t npi;      // nA + nT
     uint32_t G;        // groups (bucket, chunk) = sigma*p
+    bool grid;         // one chain per bucket on the output block grid (H = (GRID_AHEAD + 2) sigma, nT = H + 1)
 };
 
 // Device buffers of one sort, carved from one workspace allocation.
@@ -45,10 +46,19 @@ struct Bufs {
     uint32_t *LOff;    // p+1 leftover offsets
     uint32_t *state;   // scalars, see ST_*
     void *fin;         // Finalize scratch (finalize_extra_bytes)
+    // grid layout only
+    uint32_t *hist;    // nt*sigma digit counts of the input
+    uint32_t *tab;     // per-round bucket tables (4*sigma + 1 words)
+    uint32_t *status;  // look-back ring (after the rounds: Finalize's jump array and scratch)
+    uint32_t *ctr;     // per-round tile tickets
 };
 
+// grid layout: blocks a bucket's chain takes ahead of its writes (the head
+// start is (GRID_AHEAD + 2) * sigma blocks)
+constexpr uint32_t GRID_AHEAD = 2;
+
 // indices into Bufs::state
-enum { ST_F = 0, ST_NP = 1, ST_FPREV = 2, ST_LOFFTOT = 3, ST_WORDS = 8 };
+enum { ST_F = 0, ST_NP = 1, ST_FPREV = 2, ST_LOFFTOT = 3, ST_NS = 4, ST_SKIP = 5, ST_WORDS = 8 };
 
 // setup (Alg. 4) + chunk bounds of round 0
 cudaError_t launch_setup(const Geom &g, const Bufs &w, uint32_t *pi, cudaStream_t st);
@@ -59,6 +69,16 @@ cudaError_t launch_round(const Geom &g, const Bufs &w, const uint32_t *pi, const
 cudaError_t launch_fixup(const Geom &g, const Bufs &w, const uint32_t *pi_old, uint32_t *pi_new,
                          const uint32_t *UC, const uint32_t *lo_old, uint32_t *lo_new,
                          cudaStream_t st);
+// grid layout: digit histograms + setup; per round the tables and the
+// prefilled next map (prep), then sortPhase
+cudaError_t launch_grid_setup(const Geom &g, const Bufs &w, uint32_t *pi, cudaStream_t st);
+cudaError_t launch_grid_prep(const Geom &g, const Bufs &w, const uint32_t *pi, uint32_t *pin,
+                             int round, cudaStream_t st);
+cudaError_t launch_grid_round(const Geom &g, const Bufs &w, const uint32_t *pi, uint32_t *pin,
+                              int round, cudaStream_t st);
+size_t grid_ring_bytes(const Geom &g); // look-back ring of the grid layout
+// elements per tile of the look-back round kernel
+uint32_t lb_tile(int kb, int db, bool hasv);
 // gather of the logical sequence (Sec. 4.1 iterator)
 cudaError_t launch_gather(const Geom &g, const Bufs &w, const uint32_t *pi, void *out_k,
                           uint32_t *out_v, cudaStream_t st);

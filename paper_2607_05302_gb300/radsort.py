@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libradsort_gb300.so")
 
 RADSORT_OK, RADSORT_EINVAL, RADSORT_ENOMEM, RADSORT_ECUDA, RADSORT_ETIMEOUT, RADSORT_EINTERNAL = range(6)
 RADSORT_KEY_FLOAT32 = 0x1
+RADSORT_LAYOUT_AUTO, RADSORT_LAYOUT_CHUNKS, RADSORT_LAYOUT_GRID = 0, 1, 2
+LAYOUTS = {"auto": RADSORT_LAYOUT_AUTO, "chunks": RADSORT_LAYOUT_CHUNKS, "grid": RADSORT_LAYOUT_GRID}
 
 
 class RadsortError(RuntimeError):
@@ -35,7 +37,7 @@ PHASES = {0: "setup", 1: "sortPhase", 2: "fixupPhase", 3: "Finalize", 4: "key_tr
 
 class Plan(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("num_chunks", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 _lib = None
@@ -94,27 +96,35 @@ def _ok(s: int, what: str):
         raise RadsortError(s, what)
 
 
-def _plan(block_size=0, num_chunks=0):
-    if not block_size and not num_chunks:
+def _layout(layout):
+    return LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+
+
+def _plan(block_size=0, num_chunks=0, layout=0):
+    layout = _layout(layout)
+    if not block_size and not num_chunks and not layout:
         return None
     p = Plan()
     p.block_size = block_size
     p.num_chunks = num_chunks
+    p.layout = layout
     return ctypes.byref(p)
 
 
 # ---------------------------------------------------------------- raw C names
 def radsort_plan_default(n, key_bytes, value_bytes, digit_bits):
+    """(block_size, num_chunks, layout) of the automatic plan."""
     p = Plan()
     _ok(lib().radsort_plan_default(n, key_bytes, value_bytes, digit_bits, ctypes.byref(p)),
         "radsort_plan_default")
-    return int(p.block_size), int(p.num_chunks)
+    return int(p.block_size), int(p.num_chunks), int(p.layout)
 
 
-def radsort_workspace_size(n, key_bytes, value_bytes, digit_bits, block_size=0, num_chunks=0):
+def radsort_workspace_size(n, key_bytes, value_bytes, digit_bits, block_size=0, num_chunks=0,
+                           layout=0):
     out = ctypes.c_size_t(0)
     _ok(lib().radsort_workspace_size(n, key_bytes, value_bytes, digit_bits,
-                                     _plan(block_size, num_chunks), ctypes.byref(out)),
+                                     _plan(block_size, num_chunks, layout), ctypes.byref(out)),
         "radsort_workspace_size")
     return int(out.value)
 
@@ -124,16 +134,18 @@ def radsort_sort(keys, values, n, key_bytes, digit_bits, stream):
 
 
 def radsort_sort_ex(keys, values, n, key_bytes, digit_bits, flags=0, block_size=0, num_chunks=0,
-                    workspace=None, workspace_bytes=0, stream=None):
+                    workspace=None, workspace_bytes=0, stream=None, layout=0):
     _ok(lib().radsort_sort_ex(keys, values, n, key_bytes, digit_bits, flags,
-                              _plan(block_size, num_chunks), workspace, workspace_bytes, stream),
+                              _plan(block_size, num_chunks, layout), workspace, workspace_bytes,
+                              stream),
         "radsort_sort_ex")
 
 
 def radsort_sort_rounds(keys, values, n, key_bytes, digit_bits, rounds, out_keys, out_values,
-                        block_size=0, num_chunks=0, stream=None):
+                        block_size=0, num_chunks=0, stream=None, layout=0):
     _ok(lib().radsort_sort_rounds(keys, values, n, key_bytes, digit_bits, rounds,
-                                  _plan(block_size, num_chunks), out_keys, out_values, stream),
+                                  _plan(block_size, num_chunks, layout), out_keys, out_values,
+                                  stream),
         "radsort_sort_rounds")
 
 
@@ -190,7 +202,7 @@ def _ptr(t):
 
 
 def sort_tensors(keys, values=None, *, digit_bits=8, float_keys=False, block_size=0, num_chunks=0,
-                 workspace=None, stream=None):
+                 workspace=None, stream=None, layout=0):
     """In-place stable Radsort of CUDA tensors (keys: 32/64-bit, read as
     unsigned; values: optional 32-bit)."""
     assert keys.is_cuda and keys.is_contiguous()
@@ -201,14 +213,14 @@ def sort_tensors(keys, values=None, *, digit_bits=8, float_keys=False, block_siz
     ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
     radsort_sort_ex(_ptr(keys), _ptr(values), n, _key_bytes(keys), digit_bits,
                     RADSORT_KEY_FLOAT32 if float_keys else 0, block_size, num_chunks, ws, wsb,
-                    _torch_stream(stream))
+                    _torch_stream(stream), layout)
 
 
 def sort_rounds_tensors(keys, values, rounds, out_keys, out_values=None, *, digit_bits=8,
-                        block_size=0, num_chunks=0, stream=None):
+                        block_size=0, num_chunks=0, stream=None, layout=0):
     radsort_sort_rounds(_ptr(keys), _ptr(values), keys.numel(), _key_bytes(keys), digit_bits, rounds,
                         _ptr(out_keys), _ptr(out_values), block_size, num_chunks,
-                        _torch_stream(stream))
+                        _torch_stream(stream), layout)
 
 
 def lsd_oop_tensors(keys, values, keys_alt, values_alt, *, digit_bits=8, stream=None):

@@ -61,15 +61,20 @@ def test_synchronous_argument_errors(lib):
 
 
 def test_workspace_size_matches_space_analysis(lib):
-    """Sec. 3: the workspace is T (2*sigma*p blocks of b elements) plus O(n/b)
-    bookkeeping; at 2^30 8-byte elements the automatic plan stays within 2%."""
+    """Sec. 3: the workspace is the scratch array T plus O(n/b) bookkeeping.
+    The automatic plan (grid layout) has T = 4*sigma + 1 blocks and stays
+    within 2% of the array at 2^28 and 2^30 8-byte elements; the chunk layout
+    (Sec. 4.3) has T = 2*sigma*p blocks."""
     from paper_2607_05302_gb300 import radsort as R
 
-    n = 1 << 30
-    b, p = R.radsort_plan_default(n, 4, 4, 8)
-    ws = R.radsort_workspace_size(n, 4, 4, 8)
-    T = 2 * 256 * p * b * 8
-    assert T <= ws <= T + (n // b) * 64 + 256 * p * 64 + (1 << 20)
-    assert ws <= 0.02 * n * 8
+    for n in (1 << 28, 1 << 30):
+        b, p, layout = R.radsort_plan_default(n, 4, 4, 8)
+        assert layout == R.RADSORT_LAYOUT_GRID
+        ws = R.radsort_workspace_size(n, 4, 4, 8)
+        T = (4 * 256 + 1) * b * 8
+        assert T <= ws <= T + (n // b) * 16 + (n // 8192) * 256 * 4 + (1 << 20)
+        assert ws <= 0.02 * n * 8
     ws2 = R.radsort_workspace_size(1 << 20, 4, 4, 8, block_size=1024, num_chunks=2)
     assert ws2 >= 2 * 256 * 2 * 1024 * 8
+    # 2^31 elements and more: the chunk layout
+    assert R.radsort_plan_default(1 << 31, 4, 4, 8)[2] == R.RADSORT_LAYOUT_CHUNKS

@@ -22,11 +22,11 @@ def from_dev(t, dtype):
     return t.cpu().numpy().view(dtype)
 
 
-def gpu_sort(keys, vals, digit_bits=8, float_keys=False, block_size=0, num_chunks=0):
+def gpu_sort(keys, vals, digit_bits=8, float_keys=False, block_size=0, num_chunks=0, layout=0):
     kt = to_dev(keys)
     vt = None if vals is None else to_dev(vals)
     R.sort_tensors(kt, vt, digit_bits=digit_bits, float_keys=float_keys, block_size=block_size,
-                   num_chunks=num_chunks)
+                   num_chunks=num_chunks, layout=layout)
     R.radsort_device_status()
     return from_dev(kt, keys.dtype), (None if vt is None else from_dev(vt, np.uint32))
 
@@ -39,22 +39,29 @@ def oracle_sort(keys, vals, key_bits, digit_bits):
 
 
 SIZES = [2, 3, 63, 64, 65, 255, 256, 257, 4095, 4096, 4097, 10000, 65543, 300001]
-PLANS = [(64, 1), (64, 3), (256, 2), (1024, 4), (4096, 1), (0, 0), (256, 300)]
+# (block size, chunks, layout): the chunk layout of Sec. 4.3 and the grid
+# layout (one chain per bucket on the output block grid); (0, 0, auto) is the
+# automatic plan that bench.py times
+PLANS = [(64, 1, "chunks"), (64, 3, "chunks"), (256, 2, "chunks"), (1024, 4, "chunks"),
+         (4096, 1, "chunks"), (256, 300, "chunks"), (64, 0, "grid"), (256, 0, "grid"),
+         (512, 0, "grid"), (4096, 0, "grid"), (0, 0, "auto")]
+PLAN_IDS = [f"{l}-b{b}-p{p}" for b, p, l in PLANS]
 
 
-@pytest.mark.parametrize("plan", PLANS)
+@pytest.mark.parametrize("plan", PLANS, ids=PLAN_IDS)
 @pytest.mark.parametrize("n", SIZES)
 def test_u32_d8_ragged(n, plan):
     rng = np.random.default_rng(n)
     for keys in (rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32),
                  rng.integers(0, 700, n, dtype=np.uint64).astype(np.uint32)):
         vals = W.index_payload(n)
-        gk, gv = gpu_sort(keys, vals, block_size=plan[0], num_chunks=plan[1])
+        gk, gv = gpu_sort(keys, vals, block_size=plan[0], num_chunks=plan[1], layout=plan[2])
         ek, ev = oracle_sort(keys, vals, 32, 8)
         assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
 
 
-@pytest.mark.parametrize("plan", [(64, 3), (256, 5), (1024, 2)])
+@pytest.mark.parametrize("plan", [(64, 3, "chunks"), (256, 5, "chunks"), (1024, 2, "chunks"),
+                                  (64, 0, "grid"), (512, 0, "grid")])
 def test_logical_sequence_each_round(plan):
     """After r rounds the permuted representation (Sec. 4.1) read in logical
     order equals r rounds of Alg. 1 in the oracle."""
@@ -66,21 +73,24 @@ def test_logical_sequence_each_round(plan):
         kt, vt = to_dev(keys), to_dev(vals)
         ok = torch.empty_like(kt)
         ov = torch.empty_like(vt)
-        R.sort_rounds_tensors(kt, vt, r, ok, ov, digit_bits=8, block_size=plan[0], num_chunks=plan[1])
+        R.sort_rounds_tensors(kt, vt, r, ok, ov, digit_bits=8, block_size=plan[0], num_chunks=plan[1],
+                              layout=plan[2])
         R.radsort_device_status()
         lk, lv = oracle.lsd_oop(keys, vals, n_t=4, sigma=256, bits=8, rounds=r)
         assert np.array_equal(from_dev(ok, np.uint32), lk.astype(np.uint32))
         assert np.array_equal(from_dev(ov, np.uint32), lv)
 
 
+@pytest.mark.parametrize("layout", ["chunks", "grid"])
 @pytest.mark.parametrize("dist", W.DISTRIBUTIONS)
-def test_config1_distributions(dist):
+def test_config1_distributions(dist, layout):
     """n = 2^20 uint32 keys + index payload, sigma = 256, b = 1024."""
     n = 1 << 20
     keys = W.make_keys(dist, n)
     vals = W.index_payload(n)
     fl = dist == "float"
-    gk, gv = gpu_sort(keys, vals, float_keys=fl, block_size=1024, num_chunks=8)
+    gk, gv = gpu_sort(keys, vals, float_keys=fl, block_size=1024,
+                      num_chunks=8 if layout == "chunks" else 0, layout=layout)
     ok_keys = oracle.f32_to_ordered(keys) if fl else keys
     ek, ev = oracle_sort(ok_keys, vals, 32, 8)
     if fl:
@@ -90,45 +100,51 @@ def test_config1_distributions(dist):
 
 @pytest.mark.parametrize("digit_bits", [8, 11])
 @pytest.mark.parametrize("with_vals", [True, False])
-@pytest.mark.parametrize("plan", [(256, 3), (2048, 2), (0, 0)])
+@pytest.mark.parametrize("plan", [(256, 3, "chunks"), (2048, 2, "chunks"), (256, 0, "grid"),
+                                  (2048, 0, "grid"), (0, 0, "auto")])
 def test_u64(digit_bits, with_vals, plan):
     n = 200003
     keys = W.make_keys("uniform", n, 64)
     keys[::11] = keys[5]
     vals = W.index_payload(n) if with_vals else None
-    gk, gv = gpu_sort(keys, vals, digit_bits=digit_bits, block_size=plan[0], num_chunks=plan[1])
+    gk, gv = gpu_sort(keys, vals, digit_bits=digit_bits, block_size=plan[0], num_chunks=plan[1],
+                      layout=plan[2])
     ek, ev = oracle_sort(keys, vals, 64, digit_bits)
     assert np.array_equal(gk, ek)
     if with_vals:
         assert np.array_equal(gv, ev)
 
 
-@pytest.mark.parametrize("plan", [(256, 4), (512, 1)])
+@pytest.mark.parametrize("plan", [(256, 4, "chunks"), (512, 1, "chunks"), (256, 0, "grid"),
+                                  (1024, 0, "grid")])
 def test_u32_d11_and_keys_only(plan):
     n = 123457
     keys = W.make_keys("zipf", n)
-    gk, _ = gpu_sort(keys, None, digit_bits=11, block_size=plan[0], num_chunks=plan[1])
+    gk, _ = gpu_sort(keys, None, digit_bits=11, block_size=plan[0], num_chunks=plan[1], layout=plan[2])
     assert np.array_equal(gk, np.sort(keys))
     vals = W.index_payload(n)
-    gk, gv = gpu_sort(keys, vals, digit_bits=11, block_size=plan[0], num_chunks=plan[1])
+    gk, gv = gpu_sort(keys, vals, digit_bits=11, block_size=plan[0], num_chunks=plan[1],
+                      layout=plan[2])
     ek, ev = oracle_sort(keys, vals, 32, 11)
     assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
 
 
-def test_caller_workspace_and_small_n():
+@pytest.mark.parametrize("plan", [(512, 3, "chunks"), (512, 0, "grid")])
+def test_caller_workspace_and_small_n(plan):
     n = 77777
     keys = W.make_keys("reverse", n)
     vals = W.index_payload(n)
-    need = R.radsort_workspace_size(n, 4, 4, 8, block_size=512, num_chunks=3)
+    b, p, lay = plan
+    need = R.radsort_workspace_size(n, 4, 4, 8, block_size=b, num_chunks=p, layout=lay)
     ws = torch.empty(need, dtype=torch.uint8, device=DEV)
     kt, vt = to_dev(keys), to_dev(vals)
-    R.sort_tensors(kt, vt, block_size=512, num_chunks=3, workspace=ws)
+    R.sort_tensors(kt, vt, block_size=b, num_chunks=p, layout=lay, workspace=ws)
     R.radsort_device_status()
     ek, ev = oracle_sort(keys, vals, 32, 8)
     assert np.array_equal(from_dev(kt, np.uint32), ek) and np.array_equal(from_dev(vt, np.uint32), ev)
     small = torch.empty(need - 256, dtype=torch.uint8, device=DEV)
     with pytest.raises(R.RadsortError):
-        R.sort_tensors(kt, vt, block_size=512, num_chunks=3, workspace=small)
+        R.sort_tensors(kt, vt, block_size=b, num_chunks=p, layout=lay, workspace=small)
     for m in (0, 1):
         t = torch.zeros(m, dtype=torch.int32, device=DEV)
         R.sort_tensors(t, None)
@@ -169,21 +185,23 @@ def check_sorted_stable_perm(orig_keys_t, keys_t, vals_t, key_bits):
     assert bool((v[1:][eq] > v[:-1][eq]).all())
 
 
-def bench_plan():
-    """The launch configuration bench.py times: b = 256, one chunk per SM."""
+def chunk_plan():
+    """The chunk layout with one chunk per SM, b = 256 (bench.py times it
+    beside the automatic plan)."""
     return 256, torch.cuda.get_device_properties(0).multi_processor_count
 
 
-@pytest.mark.parametrize("plan", ["auto", "bench"])
+@pytest.mark.parametrize("plan", ["auto", "chunks"])
 @pytest.mark.parametrize("dist", ["uniform", "zipf", "equal", "sorted", "reverse"])
 def test_full_size_2p28_properties(dist, plan):
-    """n = 2^28 uint32 keys + index payload, in the automatic (2% memory) plan
-    and in the bench's launch configuration."""
+    """n = 2^28 uint32 keys + index payload, in the automatic plan (the grid
+    layout, bench.py's launch configuration) and in the chunk layout with one
+    chunk per SM."""
     n = 1 << 28
     keys = torch.from_numpy(W.make_keys(dist, n).view(np.int32)).to(DEV)
     vals = torch.arange(n, dtype=torch.int32, device=DEV)
     kt = keys.clone()
-    bs, pc = bench_plan() if plan == "bench" else (0, 0)
+    bs, pc = chunk_plan() if plan == "chunks" else (0, 0)
     R.sort_tensors(kt, vals, block_size=bs, num_chunks=pc)
     R.radsort_device_status()
     check_sorted_stable_perm(keys, kt, vals, 32)
@@ -195,14 +213,15 @@ def test_full_size_2p28_properties(dist, plan):
         assert pos == int((host < k).sum()) + int((host[:idx] == k).sum())
 
 
-def test_full_size_float_2p28_bench_plan():
+@pytest.mark.parametrize("plan", ["auto", "chunks"])
+def test_full_size_float_2p28(plan):
     """float32 N(0,1) keys at 2^28 through the order-preserving transform."""
     n = 1 << 28
     host = W.make_keys("float", n)
     keys = torch.from_numpy(host.view(np.int32)).to(DEV)
     vals = torch.arange(n, dtype=torch.int32, device=DEV)
     kt = keys.clone()
-    bs, pc = bench_plan()
+    bs, pc = chunk_plan() if plan == "chunks" else (0, 0)
     R.sort_tensors(kt, vals, float_keys=True, block_size=bs, num_chunks=pc)
     R.radsort_device_status()
     f = kt.view(torch.float32)
