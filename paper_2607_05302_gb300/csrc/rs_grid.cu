@@ -21,9 +21,9 @@
 //     decoupled look-back over the per-bucket counts of earlier tiles.
 //     Every other block j of bucket c is taken eagerly, as newBucketBlock
 //     does in Alg. 5 but L blocks ahead: by the tile that writes the first
-//     position of block j - L, at free-list index  nP + (blocks taken by
-//     earlier tiles) + (blocks this tile takes before it, bucket-major); the
-//     count for earlier tiles follows from E(t) alone.  A tile that continues
+//     position of block j - L, at a free-list index in  nP + (blocks taken
+//     by earlier tiles) + [0, blocks this tile takes); the count for earlier
+//     tiles follows from E(t) alone, the order within the tile is free.  A tile that continues
 //     a block therefore finds it taken long before (a bounded wait covers
 //     the rest), and tiles in flight together do not wait on each other.
 //   * The free list is the current logical order: (L+2)*sigma head-start
@@ -217,58 +217,6 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t *a, uint32_t *tmp, F &&b
     return tot;
 }
 
-// Exclusive scans of two N-element arrays at once (in place); returns both
-// totals.  tmp: 2*(NT/32)+2 words.  Ends with a barrier.
-template <int N, int NT, typename F>
-__device__ __forceinline__ uint2 block_scan2(uint32_t *a, uint32_t *c, uint32_t *tmp, F &&bar)
-{
-    constexpr int NWARP = NT / 32;
-    constexpr int IPT = (N + NT - 1) / NT;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    uint32_t va[IPT], vc[IPT], sa = 0, sc = 0;
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int idx = t * IPT + i;
-        va[i] = idx < N ? a[idx] : 0;
-        vc[i] = idx < N ? c[idx] : 0;
-        sa += va[i];
-        sc += vc[i];
-    }
-    const uint32_t ia = warp_incl_scan(sa), ic = warp_incl_scan(sc);
-    if (lane == 31) {
-        tmp[w] = ia;
-        tmp[NWARP + 1 + w] = ic;
-    }
-    bar();
-    if (w == 0) {
-        const uint32_t x = lane < NWARP ? tmp[lane] : 0, y = lane < NWARP ? tmp[NWARP + 1 + lane] : 0;
-        const uint32_t sx = warp_incl_scan(x), sy = warp_incl_scan(y);
-        if (lane < NWARP) {
-            tmp[lane] = sx - x;
-            tmp[NWARP + 1 + lane] = sy - y;
-        }
-        if (lane == 31) {
-            tmp[NWARP] = sx;
-            tmp[2 * NWARP + 1] = sy;
-        }
-    }
-    bar();
-    uint32_t ea = ia - sa + tmp[w], ec = ic - sc + tmp[NWARP + 1 + w];
-#pragma unroll
-    for (int i = 0; i < IPT; ++i) {
-        const int idx = t * IPT + i;
-        if (idx < N) {
-            a[idx] = ea;
-            c[idx] = ec;
-        }
-        ea += va[i];
-        ec += vc[i];
-    }
-    const uint2 tot = make_uint2(tmp[NWARP], tmp[2 * NWARP + 1]);
-    bar();
-    return tot;
-}
-
 // Per-round bucket offsets of the out-of-place sort: O[r][c] exclusive over
 // digits, O[r][sigma] = n (one block per digit position).
 template <int DB> __global__ void __launch_bounds__(1024) k_offsets(const uint32_t *hist, uint32_t *off, uint32_t n)
@@ -458,8 +406,10 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     static_assert(NW % TPB == 0, "rows split evenly");
     // CTAs per SM the configuration is built for (registers are capped to fit)
     static constexpr int MINB = (NW <= 8 && DB <= 8) ? 2 : 1;
-    // sigma <= 256: per-warp lane-mask table by digit (shared atomicOr);
-    // sigma = 2048: one ballot per digit bit
+    // sigma <= 256: a per-warp table of 32-bit lane masks by digit, built
+    // with shared-memory atomicOr; sigma = 2048: one ballot per digit bit.
+    // Either way a per-warp 16-bit row keeps the running count of each
+    // digit, later the warp's start per digit in the reordered tile.
     static constexpr bool PTAB = DB <= 8;
     static constexpr bool PAIR = HASV && sizeof(KT) == 4;
     static constexpr int HROW = SIGMA + 2;
@@ -475,16 +425,14 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     static constexpr size_t o_hist = o_stage + STAGES * STAGE;
     static constexpr size_t o_tab = o_hist + al(size_t(NW) * HROW * 2);
     static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * SIGMA * 4) : 0);
-    // per bucket: tcnt, bstart, gpos, O (sigma + 1); Radsort adds pk, nsb and
-    // (SMALL) ns0, ns1, sh
-    static constexpr int NBK = OOP ? 4 : (SMALL ? 9 : 6);
+    // per bucket: tcnt, bstart, gpos, O (sigma + 1); with SMALL, Radsort adds
+    // the tables ns0, ns1, sh
+    static constexpr int NBK = (!OOP && SMALL) ? 7 : 4;
     static constexpr size_t o_qb = o_bk + al((size_t(NBK) * SIGMA + 4) * 4);
     // touched blocks per tile: at most TILE/b + 2 per bucket with elements
     static constexpr int LIST = MAXM + 2 * (SIGMA < TILE ? SIGMA : TILE) + 2;
     static constexpr size_t o_lk = o_qb + al(size_t(SIGMA) * 8);
-    static constexpr size_t o_lv = o_lk + (OOP ? 0 : al(size_t(LIST) * (SMALL ? 8 : 4)));
-    static constexpr size_t o_e2b = o_lv + (!OOP && SMALL && HASV ? al(size_t(LIST) * 8) : 0);
-    static constexpr size_t o_meta = o_e2b + (OOP ? 0 : al(size_t(LIST) * 2));
+    static constexpr size_t o_meta = o_lk + (OOP ? 0 : al(size_t(LIST) * (SMALL ? 8 : 4)));
     static constexpr size_t o_bar = o_meta + al(STAGES * 16);
     static constexpr size_t o_misc = o_bar + al(2 * STAGES * 8);
     static constexpr size_t SMEM = o_misc + 512;
@@ -587,19 +535,24 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
     uint32_t *bk = reinterpret_cast<uint32_t *>(sm + C::o_bk);
     uint32_t *tcnt = bk, *bstart = bk + SIGMA, *gpos = bk + 2 * SIGMA;
     uint32_t *sO = bk + 3 * SIGMA; // sigma + 1 entries
-    uint32_t *pks = sO + SIGMA + 1, *nsb = pks + SIGMA;
+    uint32_t *stab = sO + SIGMA + 1;
     // bucket tables: shared memory (SMALL) or global
-    const uint32_t *ns0 = C::SMALL ? nsb + SIGMA : a.tab + SIGMA + 1;
+    const uint32_t *ns0 = C::SMALL ? stab : a.tab + SIGMA + 1;
     const uint32_t *ns1 = ns0 + SIGMA, *shr = ns1 + SIGMA;
     uint2 *qb = reinterpret_cast<uint2 *>(sm + C::o_qb);
-    KT **listk = reinterpret_cast<KT **>(sm + C::o_lk);
-    uint32_t **listv = reinterpret_cast<uint32_t **>(sm + C::o_lv);
+    // list entries: the key block pointer tagged with its array (SMALL), or
+    // the block index
+    unsigned long long *listk = reinterpret_cast<unsigned long long *>(sm + C::o_lk);
     uint32_t *listb = reinterpret_cast<uint32_t *>(sm + C::o_lk);
-    uint16_t *e2b = reinterpret_cast<uint16_t *>(sm + C::o_e2b); // list entry -> bucket
+    // byte distance from a key block to its value block, in T and in A
+    const long long dvT = reinterpret_cast<const char *>(a.Tv) - reinterpret_cast<const char *>(a.Tk);
+    const long long dvA = reinterpret_cast<const char *>(a.Av) - reinterpret_cast<const char *>(a.Ak);
     uint32_t *meta = reinterpret_cast<uint32_t *>(sm + C::o_meta);
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + C::o_bar);
     uint64_t *empty = full + STAGES;
-    uint32_t *misc = reinterpret_cast<uint32_t *>(sm + C::o_misc); // [0] consumed tiles, [8..] scan scratch
+    // [0] consumed tiles, [1..3] a tile's list slots, blocks taken and blocks
+    // taken by earlier tiles, [8..] scan scratch
+    uint32_t *misc = reinterpret_cast<uint32_t *>(sm + C::o_misc);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t b = 1u << a.lb;
@@ -616,9 +569,8 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
     for (int c = tid; c <= SIGMA; c += C::THREADS)
         sO[c] = a.tab[c];
     if constexpr (!OOP && C::SMALL) {
-        uint32_t *t0 = nsb + SIGMA;
         for (int c = tid; c < 3 * SIGMA; c += C::THREADS)
-            t0[c] = a.tab[SIGMA + 1 + c];
+            stab[c] = a.tab[SIGMA + 1 + c];
     }
     if constexpr (C::PTAB)
         for (int i = tid; i < NW * SIGMA; i += C::THREADS)
@@ -626,10 +578,10 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
     __syncthreads();
 
     auto kaddr = [&](uint32_t blk) -> KT * {
-        return blk < a.nT ? a.Tk + size_t(blk) * b : a.Ak + size_t(blk - a.nT) * b;
+        return blk < a.nT ? a.Tk + (size_t(blk) << a.lb) : a.Ak + (size_t(blk - a.nT) << a.lb);
     };
     auto vaddr = [&](uint32_t blk) -> uint32_t * {
-        return blk < a.nT ? a.Tv + size_t(blk) * b : a.Av + size_t(blk - a.nT) * b;
+        return blk < a.nT ? a.Tv + (size_t(blk) << a.lb) : a.Av + (size_t(blk - a.nT) << a.lb);
     };
 
     if (warp == NW) {
@@ -821,6 +773,10 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         for (int c = lane; c < SIGMA; c += 32)
             hw[c] = 0;
         if constexpr (C::PTAB) {
+            // row by row: lanes with the same digit OR their bit into the
+            // digit's mask word, read back the mask and the warp's running
+            // count; the lowest of those lanes advances the count and clears
+            // the word (the mask table is all zero between rows)
             unsigned *pt = ptab + warp * SIGMA;
             __syncwarp();
 #pragma unroll
@@ -861,15 +817,39 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         }
         bar();
 
-        // ---- 2. per-bucket warp offsets (exclusive over warps), tile counts,
-        // and this tile's counts published for the look-back
+        if (tid == 0) // this tile's slot counters (step 4)
+            misc[1] = misc[2] = misc[3] = 0u;
+
+        // ---- 2. tile counts per bucket, published for the look-back, and
+        // their exclusive scan (bucket starts in the reordered tile)
+        auto cnt_at = [&](int w, int c) -> uint32_t { return hist[w * C::HROW + c]; };
+        constexpr int RPT = NW / C::TPB;
         for (int i = tid; i < SIGMA * C::TPB; i += NT) {
             const int c = i / C::TPB, part = i % C::TPB;
-            constexpr int RPT = NW / C::TPB;
+            uint32_t sum = 0;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r)
+                sum += cnt_at(part * RPT + r, c);
+#pragma unroll
+            for (int o = C::TPB / 2; o > 0; o >>= 1)
+                sum += __shfl_xor_sync(0xffffffffu, sum, o, C::TPB);
+            if (part == C::TPB - 1) {
+                tcnt[c] = sum;
+                bstart[c] = sum;
+                st_volatile64(a.ring + size_t(t & a.rmask) * SIGMA + c,
+                              lbw(a.tagbase + t, t == 0 ? (LB_INCL | sum) : sum));
+            }
+        }
+        bar();
+        block_scan<SIGMA, NT>(bstart, tmp, bar);
+        // each warp's start per bucket in the reordered tile: bucket start +
+        // the counts of the warps before it (the ranks are warp-relative)
+        for (int i = tid; i < SIGMA * C::TPB; i += NT) {
+            const int c = i / C::TPB, part = i % C::TPB;
             uint32_t h[RPT], sum = 0;
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
-                h[r] = hist[(part * RPT + r) * C::HROW + c];
+                h[r] = cnt_at(part * RPT + r, c);
                 sum += h[r];
             }
             uint32_t incl = sum;
@@ -879,21 +859,14 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 if (part >= o)
                     incl += x;
             }
-            uint32_t run = incl - sum;
+            uint32_t run = bstart[c] + incl - sum;
 #pragma unroll
             for (int r = 0; r < RPT; ++r) {
                 hist[(part * RPT + r) * C::HROW + c] = static_cast<uint16_t>(run);
                 run += h[r];
             }
-            if (part == C::TPB - 1) {
-                tcnt[c] = incl;
-                bstart[c] = incl;
-                st_volatile64(a.ring + size_t(t & a.rmask) * SIGMA + c,
-                              lbw(a.tagbase + t, t == 0 ? (LB_INCL | incl) : incl));
-            }
         }
         bar();
-        block_scan<SIGMA, NT>(bstart, tmp, bar);
 
         // ---- 3. reorder the tile by digit, in place in its stage buffer
         // (every element is in registers since the barriers above)
@@ -901,7 +874,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         for (int it = 0; it < C::ITEMS; ++it) {
             const uint32_t d = dig[it];
             if (d < SIGMA) {
-                const uint32_t pos = bstart[d] + hist[warp * C::HROW + d] + rk[it];
+                const uint32_t pos = cnt_at(warp, d) + rk[it];
                 if constexpr (C::PAIR) {
                     tp[pos] = make_uint2(static_cast<uint32_t>(key[it]), val[it]);
                 } else {
@@ -913,8 +886,19 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         }
 
         // ---- 4. global offset of each bucket's run (look-back); Radsort:
-        // blocks touched, blocks started here, non-shared blocks started before
-        for (int c = tid; c < SIGMA; c += NT) {
+        // blocks touched, blocks taken here and by earlier tiles, list slots
+        // and free-list offsets (shared counters: the order of the blocks a
+        // tile takes does not matter, only that each index is used once), and
+        // a prefetch of the map entry of the first block touched
+        constexpr int PFN = (SIGMA + NT - 1) / NT;
+        uint32_t pf[PFN], l0s[PFN], kos[PFN];
+#pragma unroll
+        for (int q = 0; q < PFN; ++q) {
+            const int c = tid + q * NT;
+            pf[q] = PI_NONE;
+            l0s[q] = kos[q] = 0;
+            if (c >= SIGMA) // whole warps: SIGMA and NT are multiples of 32
+                continue;
             const uint32_t cn = tcnt[c];
             uint32_t excl = 0;
             if (t > 0) {
@@ -938,8 +922,22 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 const uint32_t before = mb > e0 ? mb - e0 : 0u;
                 const uint32_t f0 = max(cs, n0) + GRID_AHEAD, f1 = min(ce + GRID_AHEAD, n1);
                 const uint32_t kk = f1 > f0 ? f1 - f0 : 0u;
-                pks[c] = touched | (kk << 16);
-                nsb[c] = before;
+                // warp-aggregated slots: list entries, blocks taken, and the
+                // count of blocks taken by earlier tiles
+                const uint32_t it_ = warp_incl_scan(touched), ik = warp_incl_scan(kk);
+                const uint32_t sb = warp_sum(before);
+                uint32_t bt = 0, bk2 = 0;
+                if (lane == 31) {
+                    bt = atomicAdd(&misc[1], it_);
+                    bk2 = atomicAdd(&misc[2], ik);
+                    atomicAdd(&misc[3], sb);
+                }
+                l0s[q] = __shfl_sync(0xffffffffu, bt, 31) + it_ - touched;
+                kos[q] = __shfl_sync(0xffffffffu, bk2, 31) + ik - kk;
+                // the first block touched was taken before this tile unless
+                // this tile takes it (then its map entry is not read)
+                if (cn && (g >> a.lb) < f0)
+                    pf[q] = ld_volatile(a.pin + a.H + (g >> a.lb));
             }
         }
         bar();
@@ -948,74 +946,66 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
 
         uint32_t TT = 0; // list entries of this tile
         if constexpr (!OOP) {
-            // ---- 5. list bases and free-list offsets (packed scan), and the
-            // non-shared blocks started by earlier tiles (sum)
-            const uint2 tots = block_scan2<SIGMA, NT>(pks, nsb, tmp, bar);
-            const uint32_t ptot = tots.x, ans = tots.y;
-            TT = ptot & 0xFFFFu;
-            const uint32_t fbase = nP + ans; // free-list index of this tile's first new block
+            // ---- 5. the physical block of every block this tile touches, and
+            // the blocks it takes beyond those
+            TT = misc[1];
+            const uint32_t fbase = nP + misc[3]; // free-list index of this tile's first new block
             // free-list entries consumed so far (Lemma 1), within the list
             const uint32_t fcap = min(a.H + (t + 1) * M, a.npi);
-            for (int c = tid; c < SIGMA; c += NT) {
-                const uint32_t g = gpos[c];
-                qb[c] = make_uint2(g - bstart[c], (pks[c] & 0xFFFFu) - (g >> a.lb));
-                // blocks taken here beyond the last one this tile touches
-                const uint32_t nxt = c + 1 < SIGMA ? pks[c + 1] : ptot;
-                const uint32_t touched = (nxt & 0xFFFFu) - (pks[c] & 0xFFFFu);
-                const uint32_t kk = (nxt >> 16) - (pks[c] >> 16);
-                if (kk) {
-                    const uint32_t first = max((g + b - 1) >> a.lb, ns0[c]) + GRID_AHEAD;
-                    const uint32_t jt = (g >> a.lb) + touched; // first block not touched
-                    for (uint32_t j = max(first, jt); j < first + kk; ++j) {
-                        const uint32_t idx = fbase + (pks[c] >> 16) + (j - first);
-                        if (idx < fcap)
-                            a.pin[a.H + j] = a.pi[idx];
-                        else
-                            set_status(ST_INTERNAL); // Lemma 1 would be violated
-                    }
-                }
-                for (uint32_t i = 0; i < touched; ++i) // list entry -> bucket
-                    e2b[(pks[c] & 0xFFFFu) + i] = static_cast<uint16_t>(c);
-            }
-            bar();
-            // ---- 6. the physical block of every block this tile touches
-            for (uint32_t e = tid; e < TT; e += NT) {
-                const uint32_t c = e2b[e];
-                const uint32_t l0 = pks[c] & 0xFFFFu, ko = pks[c] >> 16;
-                const uint32_t g = gpos[c];
-                const uint32_t j = (g >> a.lb) + (e - l0);
+#pragma unroll
+            for (int q = 0; q < PFN; ++q) {
+                const int c = tid + q * NT;
+                if (c >= SIGMA)
+                    continue;
+                const uint32_t g = gpos[c], cn = tcnt[c];
+                const uint32_t l0 = l0s[q], j0 = g >> a.lb;
+                qb[c] = make_uint2(g - bstart[c], l0 - j0);
+                if (!cn)
+                    continue;
+                const uint32_t touched = ((g + cn - 1) >> a.lb) - j0 + 1;
+                const uint32_t n0 = ns0[c], n1 = ns1[c];
+                const uint32_t cs = (g + b - 1) >> a.lb, ce = (g + cn + b - 1) >> a.lb;
+                const uint32_t first = max(cs, n0) + GRID_AHEAD;
+                const uint32_t last = min(ce + GRID_AHEAD, n1); // blocks first .. last-1 taken here
                 const uint32_t sh = shr[c], fsh = sh & 0xFFFFu, lsh = sh >> 16;
-                const uint32_t n0 = ns0[c];
-                uint32_t phys;
-                if ((fsh != SH_NONE && j == (sO[c] >> a.lb)) ||
-                    (lsh != SH_NONE && j == ((sO[c + 1] - 1) >> a.lb)) || j < n0 + GRID_AHEAD) {
-                    phys = a.pin[a.H + j]; // taken before the round
-                } else {
-                    const uint32_t first = max(n0, (g + b - 1) >> a.lb) + GRID_AHEAD;
-                    if (j >= first) { // this tile writes the first position of block j - L
-                        const uint32_t idx = fbase + ko + (j - first);
-                        if (idx < fcap) {
-                            phys = a.pi[idx];
-                            a.pin[a.H + j] = phys;
-                        } else {
-                            set_status(ST_INTERNAL); // Lemma 1 would be violated
-                            phys = PI_NONE;
-                        }
-                    } else { // taken by an earlier tile
-                        phys = wait_pi(a.pin + a.H + j);
+                const uint32_t jf = sO[c] >> a.lb, jl = (sO[c + 1] - 1) >> a.lb;
+                auto take = [&](uint32_t j) -> uint32_t {
+                    const uint32_t idx = fbase + kos[q] + (j - first);
+                    if (idx >= fcap) {
+                        set_status(ST_INTERNAL); // Lemma 1 would be violated
+                        return PI_NONE;
+                    }
+                    const uint32_t ph = __ldg(a.pi + idx);
+                    a.pin[a.H + j] = ph;
+                    return ph;
+                };
+                for (uint32_t i = 0; i < touched; ++i) {
+                    const uint32_t j = j0 + i;
+                    uint32_t phys;
+                    if (j >= first && j < last && !(fsh != SH_NONE && j == jf) &&
+                        !(lsh != SH_NONE && j == jl)) {
+                        phys = take(j); // this tile writes the first position of block j - L
+                    } else { // taken before the round or by an earlier tile
+                        phys = i == 0 ? pf[q] : PI_NONE;
+                        if (phys == PI_NONE)
+                            phys = wait_pi(a.pin + a.H + j);
+                    }
+                    if (phys != PI_NONE && phys >= a.npi) {
+                        set_status(ST_INTERNAL);
+                        phys = PI_NONE;
+                    }
+                    if constexpr (C::SMALL) {
+                        // one word per entry: the key block pointer, bit 0 set
+                        // for a block of A (the value pointer follows from it)
+                        listk[l0 + i] = phys == PI_NONE ? 0ull
+                                                        : (reinterpret_cast<unsigned long long>(kaddr(phys)) |
+                                                           (phys >= a.nT ? 1ull : 0ull));
+                    } else {
+                        listb[l0 + i] = phys;
                     }
                 }
-                if (phys != PI_NONE && phys >= a.npi) {
-                    set_status(ST_INTERNAL);
-                    phys = PI_NONE;
-                }
-                if constexpr (C::SMALL) {
-                    listk[e] = phys == PI_NONE ? nullptr : kaddr(phys);
-                    if (HASV)
-                        listv[e] = phys == PI_NONE ? nullptr : vaddr(phys);
-                } else {
-                    listb[e] = phys;
-                }
+                for (uint32_t j = max(first, j0 + touched); j < last; ++j) // taken, not touched
+                    (void)take(j);
             }
             bar();
         }
@@ -1048,11 +1038,18 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 } else {
                     const uint32_t l = (pos >> a.lb) + qd.y, off = pos & (b - 1);
                     if constexpr (C::SMALL) {
-                        KT *pk = l < TT ? listk[l] : nullptr;
-                        if (pk) {
+                        const unsigned long long w = l < TT ? listk[l] : 0ull;
+                        if (w) {
+                            KT *pk = reinterpret_cast<KT *>(w & ~1ull);
                             pk[off] = kv;
-                            if (HASV)
-                                listv[l][off] = vv;
+                            if (HASV) {
+                                uint32_t *pv;
+                                if constexpr (sizeof(KT) == 4)
+                                    pv = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(pk) + ((w & 1ull) ? dvA : dvT));
+                                else
+                                    pv = ((w & 1ull) ? a.Av + (pk - a.Ak) : a.Tv + (pk - a.Tk));
+                                pv[off] = vv;
+                            }
                         }
                     } else {
                         const uint32_t blk = l < TT ? listb[l] : PI_NONE;
