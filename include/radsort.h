@@ -176,10 +176,11 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
  *
  * The workspace is a fixed array of RADSORT_NOALLOC_SCRATCH_BYTES compiled into
  * the library (every GPU that loads the library holds it until the process
- * exits).  The plan is block size 256 with as many chunks (up to one per SM)
- * as fit; an n whose workspace does not fit even with one chunk returns
- * RADSORT_ENOMEM and enqueues nothing (up to about 1.07e9 elements with
- * 4-byte keys and values fit, 8.8e8 with 8-byte keys).
+ * exits).  The plan is the automatic one (grid layout) when its workspace
+ * fits, else the chunk layout with block size 256 and as many chunks (up to
+ * one per SM) as fit; an n whose workspace does not fit even with one chunk
+ * returns RADSORT_ENOMEM and enqueues nothing (up to about 1.07e9 elements
+ * with 4-byte keys and values fit, 8.8e8 with 8-byte keys).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  No call allocates or frees memory.  All calls share the one

@@ -548,18 +548,13 @@ radsort_status radsort_sort(void *keys, uint32_t *values, size_t n, int key_byte
 
 // ---------------------------------------------------------------- segmented
 namespace {
-// plan of one large segment: block size 256, one chunk per 64K elements, at
-// most one per SM
+// plan of one large segment: the grid layout with the block size of least
+// workspace (all SMs work on the segment whatever its length)
 radsort_plan large_plan(size_t len)
 {
     radsort_plan pl{};
-    pl.block_size = 256;
-    size_t p = len / 65536;
-    if (p < 1)
-        p = 1;
-    if (p > size_t(num_sms()))
-        p = num_sms();
-    pl.num_chunks = static_cast<uint32_t>(p);
+    pl.layout = RADSORT_LAYOUT_GRID;
+    (void)len;
     return pl;
 }
 
@@ -587,7 +582,7 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
         if (seg_aligned(offh[s], kb, hasv)) {
             const radsort_plan pl = large_plan(len);
             Geom g;
-            if (fill_geom(len, kb, hasv, db, pl.block_size, pl.num_chunks, &g) != RADSORT_OK)
+            if (make_geom(len, kb, hasv, db, &pl, &g) != RADSORT_OK)
                 return RADSORT_EINVAL;
             need = layout(g, nullptr, nullptr);
         } else { // out of place, Alg. 1, with alternate buffers in the workspace
@@ -715,13 +710,22 @@ radsort_status noalloc_scratch(void **out)
     return RADSORT_OK;
 }
 
-// block size 256 and as many chunks (up to one per SM) as fit in the scratch
+// the automatic plan (grid layout) when its workspace fits in the scratch;
+// otherwise the chunk layout with block size 256 and as many chunks (up to
+// one per SM) as fit
 radsort_status noalloc_plan(size_t n, int kb, bool hasv, int db, radsort_plan *pl)
 {
     std::memset(pl, 0, sizeof(*pl));
+    Geom g;
+    if (make_geom(n, kb, hasv, db, nullptr, &g) == RADSORT_OK && g.grid &&
+        layout(g, nullptr, nullptr) <= RADSORT_NOALLOC_SCRATCH_BYTES) {
+        pl->layout = RADSORT_LAYOUT_GRID;
+        pl->block_size = g.b;
+        return RADSORT_OK;
+    }
+    pl->layout = RADSORT_LAYOUT_CHUNKS;
     pl->block_size = 256;
     uint32_t lo = 1, hi = static_cast<uint32_t>(num_sms());
-    Geom g;
     if (fill_geom(n, kb, hasv, db, 256, 1, &g) != RADSORT_OK ||
         layout(g, nullptr, nullptr) > RADSORT_NOALLOC_SCRATCH_BYTES)
         return RADSORT_ENOMEM; // n too large for the fixed scratch

@@ -814,7 +814,8 @@ FinLayout fin_layout(const Geom &g)
 {
     FinLayout L{};
     const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
-    uint32_t K = static_cast<uint32_t>((64u << 10) / bbytes);
+    // strides of 32 KB: several CTAs per SM keep enough bytes in flight
+    uint32_t K = static_cast<uint32_t>((32u << 10) / bbytes);
     if (K > 32)
         K = 32; // one warp issues the bulk copies, one entry per lane
     if (K < 2)
