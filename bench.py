@@ -165,33 +165,40 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def round_kernel_hash():
-    """Hash of the round kernel's source: a traffic figure taken with ncu on an
+# committed ncu summary of each layout's round kernel, and the sources it covers
+ROUND_PROFILES = {
+    "grid": ("k_lb_round_grid_u32kv_d8_ncu.md", ("rs_grid.cu", "rs_common.cuh", "rs_kernels.cuh")),
+    "chunks": ("k_round_u32kv_d8_ncu.md", ("rs_round.cu", "rs_common.cuh", "rs_kernels.cuh")),
+}
+
+
+def round_kernel_hash(files):
+    """Hash of a round kernel's sources: a traffic figure taken with ncu on an
     older kernel is not reported."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("rs_round.cu", "rs_common.cuh", "rs_kernels.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2607_05302_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n, kb, db):
-    """DRAM bytes per k_round launch (dram__bytes_read.sum + write.sum) from
-    the committed ncu summary, scaled from the captured size to n by the
-    elements processed; None if the summary is missing or older than the
-    kernel."""
-    path = os.path.join(ROOT, "profiles", "k_round_u32kv_d8_ncu.md")
+def profiled_traffic(n, kb, db, lay):
+    """DRAM bytes per round-kernel launch (dram__bytes_read.sum + write.sum)
+    from the committed ncu summary of the layout's kernel, scaled from the
+    captured size to n by the elements processed; None if the summary is
+    missing or older than the kernel."""
+    name, files = ROUND_PROFILES["chunks" if lay == "chunks" else "grid"]
     try:
-        txt = open(path).read()
+        txt = open(os.path.join(ROOT, "profiles", name)).read()
     except OSError:
         return None
     import re
 
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_element:\s*([0-9.]+)", txt)
-    if not m or not t or m.group(1) != round_kernel_hash() or kb != 4 or db != 8:
+    if not m or not t or m.group(1) != round_kernel_hash(files) or kb != 4 or db != 8:
         return None
     return round(float(t.group(1)) * n)
 
@@ -448,7 +455,7 @@ def main():
     avg_round = statistics.mean(round_ms) if round_ms else float("nan")
     hbm, src = peaks()
     achieved = (n * 2 * E) / (avg_round / 1e3) / 1e9
-    traffic = profiled_traffic(n, kb, db)
+    traffic = profiled_traffic(n, kb, db, lay)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "kernel": ("k_round (sortPhase, Alg. 5, chunk layout)" if lay == "chunks"

@@ -171,25 +171,34 @@ static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32
 static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl);
 
 // Automatic plan: the grid layout (its extra memory does not grow with the
-// number of CTAs) with the block size of least workspace; the chunk layout
-// (Sec. 4.3) when n >= 2^31 or when the plan asks for it.
+// number of CTAs); the chunk layout (Sec. 4.3) when n >= 2^31 or when the
+// plan asks for it.  Larger blocks are faster (fewer list entries and bulk
+// copies per tile, fewer blocks to permute in Finalize) but the scratch array
+// grows with b, so the plan takes the largest block size whose workspace is
+// within 2% of the array's bytes, or within 1.25x the least workspace of any
+// block size when no block size meets 2%.
 static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
 {
     const long el = env_long("RADSORT_LAYOUT", 0);
     const uint32_t want = pl->layout ? pl->layout : static_cast<uint32_t>(el);
     if (want != RADSORT_LAYOUT_CHUNKS && n < (size_t(1) << 31)) {
-        uint32_t best_b = 0;
-        size_t best = 0;
-        for (uint32_t b : {512u, 1024u, 256u, 2048u}) {
+        const uint32_t cands[] = {256, 512, 1024, 2048, 4096};
+        size_t ws[5] = {};
+        size_t least = 0;
+        for (int i = 0; i < 5; ++i) {
             Geom g;
-            if (fill_geom_grid(n, kb, vb != 0, db, b, &g) != RADSORT_OK)
+            if (fill_geom_grid(n, kb, vb != 0, db, cands[i], &g) != RADSORT_OK)
                 continue;
-            const size_t sz = layout(g, nullptr, nullptr);
-            if (!best_b || sz < best) {
-                best = sz;
-                best_b = b;
-            }
+            ws[i] = layout(g, nullptr, nullptr);
+            if (!least || ws[i] < least)
+                least = ws[i];
         }
+        const double two = 0.02 * double(n) * double(kb + vb);
+        const double budget = two > 1.25 * double(least) ? two : 1.25 * double(least);
+        uint32_t best_b = 0;
+        for (int i = 0; i < 5; ++i)
+            if (ws[i] && double(ws[i]) <= budget)
+                best_b = cands[i];
         if (best_b) {
             pl->layout = RADSORT_LAYOUT_GRID;
             pl->block_size = best_b;
