@@ -62,13 +62,21 @@ typedef enum {
  *    by the buckets in them).  All SMs work on it through a decoupled
  *    look-back; T holds 4*sigma + 1 blocks whatever the parallelism, and
  *    after the last round every block but the tail is full.  Needs n < 2^31.
+ *  RADSORT_LAYOUT_SCRATCH: short arrays are sorted out of place (Alg. 1) with
+ *    the alternate arrays inside the workspace, the paper's suggestion for
+ *    arrays below Radsort's crossover (Sec. 5: use T as A').  The automatic
+ *    plan takes it for n <= RADSORT_SCRATCH_MAX_N; radsort_sort_rounds never
+ *    uses it.
  */
 #define RADSORT_LAYOUT_AUTO 0u
 #define RADSORT_LAYOUT_CHUNKS 1u
 #define RADSORT_LAYOUT_GRID 2u
+#define RADSORT_LAYOUT_SCRATCH 3u
+#define RADSORT_SCRATCH_MAX_N ((size_t)1 << 18)
 
-/* Tuning plan.  Zero fields mean "choose automatically" (the grid layout
- * when n < 2^31, with the block size of least workspace). */
+/* Tuning plan.  Zero fields mean "choose automatically": the scratch layout
+ * up to RADSORT_SCRATCH_MAX_N elements, the grid layout below 2^31 (largest
+ * block size within 2% of the array's bytes), the chunk layout beyond. */
 typedef struct {
     uint32_t block_size; /* b: elements per block, power of two in [64, 4096] */
     uint32_t num_chunks; /* p (chunk layout): chunks sorted in parallel, each

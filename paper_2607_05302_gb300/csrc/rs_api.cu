@@ -271,10 +271,10 @@ static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radso
 {
     if ((kb != 4 && kb != 8) || (db != 8 && db != 11))
         return RADSORT_EINVAL;
-    if (plan && plan->layout > RADSORT_LAYOUT_GRID)
+    if (plan && plan->layout > RADSORT_LAYOUT_SCRATCH)
         return RADSORT_EINVAL;
     radsort_plan pl{};
-    if (plan)
+    if (plan && plan->layout != RADSORT_LAYOUT_SCRATCH)
         pl.layout = plan->layout;
     // a chunk count without a layout means the chunk layout
     if (plan && plan->num_chunks && !plan->layout)
@@ -347,6 +347,26 @@ static size_t layout(const Geom &g, void *base, Bufs *w)
 }
 
 static cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+// The scratch layout: a full sort of a short array (or an explicit request)
+// runs Alg. 1 with the alternate arrays inside the workspace.
+static bool use_scratch(size_t n, const radsort_plan *plan, bool full_sort)
+{
+    if (!full_sort)
+        return false;
+    if (plan && plan->layout == RADSORT_LAYOUT_SCRATCH)
+        return true;
+    const bool automatic = !plan || (plan->layout == RADSORT_LAYOUT_AUTO && !plan->block_size &&
+                                     !plan->num_chunks);
+    return automatic && n <= RADSORT_SCRATCH_MAX_N;
+}
+
+// [alternate keys | alternate values | Alg. 1 scratch]
+static size_t scratch_bytes(size_t n, int kb, bool hasv, int db)
+{
+    return align_up(n * kb, 256) + (hasv ? align_up(n * 4, 256) : 0) +
+           align_up(lsd_oop_scratch_bytes(n, kb, db, hasv), 256);
+}
 
 static radsort_status cuda_status(cudaError_t e)
 {
@@ -445,6 +465,10 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
         (digit_bits != 8 && digit_bits != 11))
         return RADSORT_EINVAL;
     std::memset(plan, 0, sizeof(*plan));
+    if (n <= RADSORT_SCRATCH_MAX_N) {
+        plan->layout = RADSORT_LAYOUT_SCRATCH;
+        return RADSORT_OK;
+    }
     auto_plan(n, key_bytes, value_bytes, digit_bits, plan);
     return RADSORT_OK;
 }
@@ -457,6 +481,12 @@ radsort_status radsort_workspace_size(size_t n, int key_bytes, int value_bytes, 
     *bytes = 0;
     if (n <= 1)
         return RADSORT_OK;
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (use_scratch(n, plan, true)) {
+        *bytes = scratch_bytes(n, key_bytes, value_bytes == 4, digit_bits);
+        return RADSORT_OK;
+    }
     Geom g;
     radsort_status s = make_geom(n, key_bytes, value_bytes == 4, digit_bits, plan, &g);
     if (s != RADSORT_OK)
@@ -480,6 +510,47 @@ static radsort_status sort_common(void *keys, uint32_t *values, size_t n, int ke
         return RADSORT_OK;
     if (!keys || !aligned16(keys) || (values && !aligned16(values)))
         return RADSORT_EINVAL;
+    if (plan && plan->layout == RADSORT_LAYOUT_SCRATCH && rounds >= 0)
+        return RADSORT_EINVAL; // no permuted representation to read
+    if (use_scratch(n, plan, rounds < 0)) {
+        cudaStream_t st = as_stream(stream);
+        const bool hasv = values != nullptr;
+        const size_t need = scratch_bytes(n, key_bytes, hasv, digit_bits);
+        void *ws = workspace;
+        bool own = false;
+        if (ws) {
+            if (workspace_bytes < need || !aligned16(ws))
+                return workspace_bytes < need ? RADSORT_ENOMEM : RADSORT_EINVAL;
+        } else {
+            cudaError_t e = cudaMallocAsync(&ws, need, st);
+            if (e != cudaSuccess)
+                return cuda_status(e);
+            own = true;
+        }
+        char *ak = static_cast<char *>(ws);
+        char *av = ak + align_up(n * key_bytes, 256);
+        char *sc = av + (hasv ? align_up(n * 4, 256) : 0);
+        cudaError_t e = cudaSuccess;
+        if (flags & RADSORT_KEY_FLOAT32) {
+            Scope sc0(4, -1, st);
+            e = launch_float_keys(static_cast<uint32_t *>(keys), n, 0, st);
+        }
+        if (e == cudaSuccess) {
+            Scope sc1(1, -1, st);
+            e = launch_lsd_oop_ws(keys, values, ak, hasv ? reinterpret_cast<uint32_t *>(av) : nullptr, n,
+                                  key_bytes, digit_bits, sc, st);
+        }
+        if (e == cudaSuccess && (flags & RADSORT_KEY_FLOAT32)) {
+            Scope sc2(4, -1, st);
+            e = launch_float_keys(static_cast<uint32_t *>(keys), n, 1, st);
+        }
+        if (own) {
+            cudaError_t e2 = cudaFreeAsync(ws, st);
+            if (e == cudaSuccess)
+                e = e2;
+        }
+        return cuda_status(e);
+    }
     Geom g;
     radsort_status s = make_geom(n < 2 ? 2 : n, key_bytes, values != nullptr, digit_bits, plan, &g);
     if (s != RADSORT_OK)

@@ -78,3 +78,16 @@ def test_workspace_size_matches_space_analysis(lib):
     assert ws2 >= 2 * 256 * 2 * 1024 * 8
     # 2^31 elements and more: the chunk layout
     assert R.radsort_plan_default(1 << 31, 4, 4, 8)[2] == R.RADSORT_LAYOUT_CHUNKS
+
+
+def test_plan_layouts_by_size(lib):
+    """Short arrays: out of place with the alternate arrays in the workspace
+    (Sec. 5); up to 2^31: the grid layout; beyond: the chunk layout."""
+    from paper_2607_05302_gb300 import radsort as R
+
+    n = R.RADSORT_SCRATCH_MAX_N
+    assert R.radsort_plan_default(n, 4, 4, 8)[2] == R.RADSORT_LAYOUT_SCRATCH
+    assert R.radsort_plan_default(n + 1, 4, 4, 8)[2] == R.RADSORT_LAYOUT_GRID
+    # the scratch workspace holds the alternate keys and values
+    assert R.radsort_workspace_size(n, 4, 4, 8) >= n * 8
+    assert R.radsort_workspace_size(n, 4, 4, 8, layout="grid") < R.radsort_workspace_size(n, 4, 4, 8) + (16 << 20)

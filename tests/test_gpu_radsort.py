@@ -44,7 +44,7 @@ SIZES = [2, 3, 63, 64, 65, 255, 256, 257, 4095, 4096, 4097, 10000, 65543, 300001
 # automatic plan that bench.py times
 PLANS = [(64, 1, "chunks"), (64, 3, "chunks"), (256, 2, "chunks"), (1024, 4, "chunks"),
          (4096, 1, "chunks"), (256, 300, "chunks"), (64, 0, "grid"), (256, 0, "grid"),
-         (512, 0, "grid"), (4096, 0, "grid"), (0, 0, "auto")]
+         (512, 0, "grid"), (4096, 0, "grid"), (0, 0, "scratch"), (0, 0, "auto")]
 PLAN_IDS = [f"{l}-b{b}-p{p}" for b, p, l in PLANS]
 
 
@@ -81,7 +81,7 @@ def test_logical_sequence_each_round(plan):
         assert np.array_equal(from_dev(ov, np.uint32), lv)
 
 
-@pytest.mark.parametrize("layout", ["chunks", "grid"])
+@pytest.mark.parametrize("layout", ["chunks", "grid", "scratch"])
 @pytest.mark.parametrize("dist", W.DISTRIBUTIONS)
 def test_config1_distributions(dist, layout):
     """n = 2^20 uint32 keys + index payload, sigma = 256, b = 1024."""
@@ -129,13 +129,14 @@ def test_u32_d11_and_keys_only(plan):
     assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
 
 
-@pytest.mark.parametrize("plan", [(512, 3, "chunks"), (512, 0, "grid")])
+@pytest.mark.parametrize("plan", [(512, 3, "chunks"), (512, 0, "grid"), (0, 0, "scratch")])
 def test_caller_workspace_and_small_n(plan):
     n = 77777
     keys = W.make_keys("reverse", n)
     vals = W.index_payload(n)
     b, p, lay = plan
     need = R.radsort_workspace_size(n, 4, 4, 8, block_size=b, num_chunks=p, layout=lay)
+    assert need >= (n * 8 if lay == "scratch" else 0)
     ws = torch.empty(need, dtype=torch.uint8, device=DEV)
     kt, vt = to_dev(keys), to_dev(vals)
     R.sort_tensors(kt, vt, block_size=b, num_chunks=p, layout=lay, workspace=ws)
