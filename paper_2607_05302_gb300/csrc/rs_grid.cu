@@ -156,22 +156,93 @@ __global__ void __launch_bounds__(512) k_digit_hist(const KT *keys, uint32_t n, 
             atomicAdd(&hist[i], sh[i]);
 }
 
-// Launches k_digit_hist for the key and digit widths.
+// 8-bit digits: counts of four digit positions r0 .. r0+3 with one counter
+// column per lane (counter (r, d) of lane l at word (r*256 + d)*32 + l), so
+// the 32 atomics of a warp instruction fall in 32 different banks whatever
+// the digits.  One CTA of 1024 threads per SM, 128 KB of counters.
+template <typename KT>
+__global__ void __launch_bounds__(1024) k_digit_hist_lanes(const KT *keys, uint32_t n, int r0, uint32_t *hist)
+{
+    constexpr int NTD = 8 * int(sizeof(KT)) / 8;
+    constexpr int G = 4; // digit positions per pass
+    constexpr int V = 16 / sizeof(KT);
+    extern __shared__ uint32_t sh[]; // G * 256 * 32
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < G * 256 * 32; i += blockDim.x)
+        sh[i] = 0;
+    __syncthreads();
+    const int npos = min(G, NTD - r0);
+    auto put = [&](KT k) {
+#pragma unroll
+        for (int r = 0; r < G; ++r)
+            if (r < npos)
+                atomicAdd(&sh[(r * 256 + digit_of(k, uint32_t((r0 + r) * 8), 255u)) * 32 + lane], 1u);
+    };
+    const size_t stride = size_t(gridDim.x) * blockDim.x;
+    const size_t first = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    const size_t nv = vec ? n / V : 0;
+    const uint4 *kv = reinterpret_cast<const uint4 *>(keys);
+    constexpr int U = 4;
+    for (size_t i = first; i < nv; i += U * stride) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i + u * stride < nv)
+                v[u] = kv[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i + u * stride < nv) {
+                KT k[V];
+                memcpy(k, &v[u], 16);
+#pragma unroll
+                for (int q = 0; q < V; ++q)
+                    put(k[q]);
+            }
+    }
+    for (size_t i = nv * V + first; i < n; i += stride)
+        put(keys[i]);
+    __syncthreads();
+    // per (position, digit): the sum of the 32 lane columns
+    for (int i = threadIdx.x; i < npos * 256; i += blockDim.x) {
+        const uint32_t *row = sh + size_t(i) * 32;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int l = 0; l < 32; ++l)
+            sum += row[(l + i) & 31]; // rotated start: consecutive threads, different banks
+        if (sum)
+            atomicAdd(&hist[(r0 + i / 256) * 256 + (i % 256)], sum);
+    }
+}
+
+// Launches the digit histograms for the key and digit widths.
 static void launch_digit_hist(const void *keys, uint32_t n, int kb, int db, uint32_t *hist, cudaStream_t st)
 {
-    const int grid = num_sms() * 2;
-    if (kb == 4) {
-        if (db == 8)
-            k_digit_hist<uint32_t, 8><<<grid, 512, 4 * 256 * 4, st>>>(static_cast<const uint32_t *>(keys), n, hist);
-        else
-            k_digit_hist<uint32_t, 11><<<grid, 512, 3 * 2048 * 4, st>>>(static_cast<const uint32_t *>(keys), n, hist);
-    } else {
-        using u64 = unsigned long long;
-        if (db == 8)
-            k_digit_hist<u64, 8><<<grid, 512, 8 * 256 * 4, st>>>(static_cast<const u64 *>(keys), n, hist);
-        else
-            k_digit_hist<u64, 11><<<grid, 512, 6 * 2048 * 4, st>>>(static_cast<const u64 *>(keys), n, hist);
+    using u64 = unsigned long long;
+    if (db == 8) {
+        constexpr int LSM = 4 * 256 * 32 * 4;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_digit_hist_lanes<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, LSM);
+            cudaFuncSetAttribute(k_digit_hist_lanes<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, LSM);
+            attr = true;
+        }
+        const int grid = num_sms();
+        if (kb == 4) {
+            k_digit_hist_lanes<uint32_t><<<grid, 1024, LSM, st>>>(static_cast<const uint32_t *>(keys), n, 0, hist);
+            g_launches += 1;
+        } else {
+            for (int r0 = 0; r0 < 8; r0 += 4)
+                k_digit_hist_lanes<u64><<<grid, 1024, LSM, st>>>(static_cast<const u64 *>(keys), n, r0, hist);
+            g_launches += 2;
+        }
+        return;
     }
+    const int grid = num_sms() * 2;
+    if (kb == 4)
+        k_digit_hist<uint32_t, 11><<<grid, 512, 3 * 2048 * 4, st>>>(static_cast<const uint32_t *>(keys), n, hist);
+    else
+        k_digit_hist<u64, 11><<<grid, 512, 6 * 2048 * 4, st>>>(static_cast<const u64 *>(keys), n, hist);
     g_launches += 1;
 }
 
