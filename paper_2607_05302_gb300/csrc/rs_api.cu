@@ -137,7 +137,7 @@ static radsort_status fill_geom(size_t n, int kb, bool hasv, int db, uint32_t b,
 // holds the input tail), the data in logical blocks H .. H + nA.
 static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32_t b, Geom *g)
 {
-    if (!pow2(b) || b < 64 || b > 4096 || b > lb_tile(kb, db, hasv))
+    if (!pow2(b) || b < 64 || b > 4096 || lb_tile(kb, db, hasv) % b != 0)
         return RADSORT_EINVAL; // a tile holds whole blocks
     if (n >= (size_t(1) << 31))
         return RADSORT_EINVAL; // look-back words hold 31-bit prefixes

@@ -475,6 +475,9 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     static_assert(THREADS <= 1024, "one CTA holds at most 1024 threads");
     static constexpr int TPB = NW >= 16 ? 4 : (NW >= 4 ? 2 : 1);
     static_assert(NW % TPB == 0, "rows split evenly");
+    // more than 16 elements per thread: digits are recomputed from the keys
+    // and warp ranks kept as 16-bit halves, to stay within the registers
+    static constexpr bool LEAN = ITEMS > 16;
     // CTAs per SM the configuration is built for (registers are capped to fit)
     static constexpr int MINB = (NW <= 8 && DB <= 8) ? 2 : 1;
     // sigma <= 256: a per-warp table of 32-bit lane masks by digit, built
@@ -830,14 +833,37 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
 
         // ---- 1. this thread's elements into registers; stable rank within the warp
         KT key[C::ITEMS];
-        uint32_t val[C::ITEMS], dig[C::ITEMS], rk[C::ITEMS];
+        uint32_t val[C::ITEMS];
+        uint32_t digs[C::LEAN ? 1 : C::ITEMS];
+        uint32_t rks[C::LEAN ? (C::ITEMS + 1) / 2 : C::ITEMS];
+        // digit of item it (SIGMA past the tile's end) and its rank in the warp
+        auto dig = [&](int it) -> uint32_t {
+            if constexpr (C::LEAN)
+                return warp * C::R + it * 32 + lane < cnt ? digit_of(key[it], a.shift, mask)
+                                                          : uint32_t(SIGMA);
+            else
+                return digs[it];
+        };
+        auto set_rk = [&](int it, uint32_t v) {
+            if constexpr (C::LEAN)
+                rks[it >> 1] = (it & 1) ? ((rks[it >> 1] & 0xFFFFu) | (v << 16)) : ((rks[it >> 1] & 0xFFFF0000u) | v);
+            else
+                rks[it] = v;
+        };
+        auto get_rk = [&](int it) -> uint32_t {
+            if constexpr (C::LEAN)
+                return (it & 1) ? (rks[it >> 1] >> 16) : (rks[it >> 1] & 0xFFFFu);
+            else
+                return rks[it];
+        };
 #pragma unroll
         for (int it = 0; it < C::ITEMS; ++it) {
             const uint32_t e = warp * C::R + it * 32 + lane;
             key[it] = tk[leadk + e];
             if (HASV)
                 val[it] = tv[leadv + e];
-            dig[it] = e < cnt ? digit_of(key[it], a.shift, mask) : uint32_t(SIGMA);
+            if constexpr (!C::LEAN)
+                digs[it] = e < cnt ? digit_of(key[it], a.shift, mask) : uint32_t(SIGMA);
         }
         const unsigned lt = lanemask_lt();
         uint16_t *hw = hist + warp * C::HROW;
@@ -852,14 +878,14 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             __syncwarp();
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it) {
-                const uint32_t d = dig[it];
+                const uint32_t d = dig(it);
                 const bool v = d < SIGMA;
                 if (v)
                     atomicOr(&pt[d], 1u << lane);
                 __syncwarp();
                 const unsigned pm = v ? pt[d] : 0u;
                 const uint32_t base = v ? hw[d] : 0u;
-                rk[it] = base + __popc(pm & lt);
+                set_rk(it, base + __popc(pm & lt));
                 __syncwarp();
                 if (v && (__ffs(pm) - 1) == lane) {
                     hw[d] = static_cast<uint16_t>(base + __popc(pm));
@@ -871,15 +897,15 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             unsigned peers[C::ITEMS];
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it)
-                peers[it] = peer_mask<DB>(dig[it], dig[it] < SIGMA);
+                peers[it] = peer_mask<DB>(dig(it), dig(it) < SIGMA);
             __syncwarp();
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it) {
-                const uint32_t d = dig[it];
+                const uint32_t d = dig(it);
                 uint32_t base = 0;
                 if (d < SIGMA)
                     base = hw[d];
-                rk[it] = base + __popc(peers[it] & lt);
+                set_rk(it, base + __popc(peers[it] & lt));
                 __syncwarp();
                 if (d < SIGMA && (__ffs(peers[it]) - 1) == lane)
                     hw[d] = static_cast<uint16_t>(base + __popc(peers[it]));
@@ -943,9 +969,9 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         // (every element is in registers since the barriers above)
 #pragma unroll
         for (int it = 0; it < C::ITEMS; ++it) {
-            const uint32_t d = dig[it];
+            const uint32_t d = dig(it);
             if (d < SIGMA) {
-                const uint32_t pos = cnt_at(warp, d) + rk[it];
+                const uint32_t pos = cnt_at(warp, d) + get_rk(it);
                 if constexpr (C::PAIR) {
                     tp[pos] = make_uint2(static_cast<uint32_t>(key[it]), val[it]);
                 } else {
@@ -1166,16 +1192,19 @@ static int lb_ctas(size_t ntiles)
 template <typename F> static cudaError_t lb_dispatch(int kb, int db, bool hasv, F &&f)
 {
     using u64 = unsigned long long;
+    // 8-bit digits: the largest tiles that two stages and the tables leave
+    // room for (per-tile costs scale with sigma, not with the tile), each a
+    // multiple of 2048 so that blocks of up to 2048 elements fit whole
     if (kb == 4) {
         if (db == 8)
-            return hasv ? f.template operator()<uint32_t, true, 8, 8192, 16, 2>()
-                        : f.template operator()<uint32_t, false, 8, 8192, 16, 3>();
+            return hasv ? f.template operator()<uint32_t, true, 8, 10240, 16, 2>()
+                        : f.template operator()<uint32_t, false, 8, 16384, 16, 2>();
         return hasv ? f.template operator()<uint32_t, true, 11, 4096, 8, 2>()
                     : f.template operator()<uint32_t, false, 11, 4096, 8, 3>();
     }
     if (db == 8)
-        return hasv ? f.template operator()<u64, true, 8, 4096, 16, 3>()
-                    : f.template operator()<u64, false, 8, 8192, 16, 2>();
+        return hasv ? f.template operator()<u64, true, 8, 6144, 16, 2>()
+                    : f.template operator()<u64, false, 8, 10240, 16, 2>();
     return hasv ? f.template operator()<u64, true, 11, 2048, 8, 3>()
                 : f.template operator()<u64, false, 11, 4096, 8, 2>();
 }

@@ -44,7 +44,7 @@ SIZES = [2, 3, 63, 64, 65, 255, 256, 257, 4095, 4096, 4097, 10000, 65543, 300001
 # automatic plan that bench.py times
 PLANS = [(64, 1, "chunks"), (64, 3, "chunks"), (256, 2, "chunks"), (1024, 4, "chunks"),
          (4096, 1, "chunks"), (256, 300, "chunks"), (64, 0, "grid"), (256, 0, "grid"),
-         (512, 0, "grid"), (4096, 0, "grid"), (0, 0, "scratch"), (0, 0, "auto")]
+         (512, 0, "grid"), (2048, 0, "grid"), (0, 0, "scratch"), (0, 0, "auto")]
 PLAN_IDS = [f"{l}-b{b}-p{p}" for b, p, l in PLANS]
 
 
