@@ -203,6 +203,19 @@ def profiled_traffic(n, kb, db, lay):
     return round(float(t.group(1)) * n)
 
 
+def replica_result(ms, n, steps, world, dist, device):
+    """Replicas (one independent sort per rank): the slowest rank's time for
+    `steps` sorts, and the whole job's keys per second over that time
+    (Gkeys/s).  dist is torch.distributed (None for one process)."""
+    import torch
+
+    tmax = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    return ms_max, world * steps * n / (ms_max / 1e3) / 1e9
+
+
 def oop_scratch_bytes(n, kb, db):
     """Scratch of the out-of-place comparator besides its alternate arrays:
     digit histograms and offsets, and the look-back ring (R tiles x sigma
@@ -441,11 +454,7 @@ def main():
     clk = clocks.stop()
     R.radsort_device_status()
     recs = R.radsort_trace_read()
-    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * a.steps * n / (ms_max / 1e3) / 1e9
+    ms_max, value = replica_result(ms, n, a.steps, world, dist, dev)
 
     phases = {}
     for ph, rd, t in recs:
