@@ -8,7 +8,9 @@ Finalize.  Every timed step sorts its own fresh copy of the input (2 GiB,
 larger than L2), made before the timed region.
 
 Printed as one JSON line: device-resident throughput (value), end-to-end
-throughput through the public call with host buffers (e2e), the roofline of
+throughput through the public call with pinned host buffers, copies in and
+out inside the timed region, steps overlapped on three streams (e2e; the
+one-stream figure beside it), the roofline of
 the dominant kernel (the sortPhase round kernel, CUDA events on its stream),
 the out-of-place LSD comparator on the same data and GPU, extra device bytes,
 clocks sampled during the timed region, and the oracle timed on the host
@@ -231,11 +233,18 @@ def oop_scratch_bytes(n, kb, db):
     return al(nt * sigma * 4) + al(nt * (sigma + 1) * 4) + al(rows * sigma * 8 + rows * 4) + al(256)
 
 
-def end_to_end(a, R, keys0, vals0, dk, dv, n, kb, db, E, world, barrier, stream):
+def end_to_end(a, R, keys0, vals0, kbufs, vbufs, n, kb, db, E, world, barrier, stream):
     """Same metric through the public call radsort_sort with pinned host
-    buffers: H2D of the inputs, the sort, D2H of the result, every step."""
+    buffers.  Every step copies its inputs host -> device, sorts them with
+    radsort_sort (automatic plan, allocating) and copies the sorted keys and
+    values device -> host, all inside the timed region.  The steps run on
+    `depth` streams, each with its own device and host output buffers, so
+    the copies of one step overlap the sort of another (copy engines and SMs
+    work side by side), as a batch of independent requests would run; the
+    same steps on one stream, nothing overlapped, are reported as `serial`."""
     import ctypes
 
+    import numpy as np
     import torch
 
     ktype = keys0.dtype
@@ -243,31 +252,59 @@ def end_to_end(a, R, keys0, vals0, dk, dv, n, kb, db, E, world, barrier, stream)
     hv = torch.empty(n, dtype=torch.int32, pin_memory=True)
     hk.copy_(keys0.cpu())
     hv.copy_(vals0.cpu())
-    ok_ = torch.empty_like(hk, pin_memory=True)
-    ov_ = torch.empty_like(hv, pin_memory=True)
-    steps = max(2, min(a.steps, 5))
+    depth = max(1, min(3, len(kbufs)))
+    outs = [(torch.empty(n, dtype=ktype, pin_memory=True), torch.empty(n, dtype=torch.int32, pin_memory=True))
+            for _ in range(depth)]
+    if not all(t.is_pinned() for t in [hk, hv] + [t for o in outs for t in o]):
+        raise SystemExit("bench: host buffers are not pinned")
+    streams = [torch.cuda.Stream() for _ in range(depth)]
 
-    def step():
-        dk.copy_(hk, non_blocking=True)
-        dv.copy_(hv, non_blocking=True)
-        R.radsort_sort(ctypes.c_void_p(dk.data_ptr()), ctypes.c_void_p(dv.data_ptr()), n, kb, db,
-                       R._torch_stream(None))
-        ok_.copy_(dk, non_blocking=True)
-        ov_.copy_(dv, non_blocking=True)
+    def step(s, d):
+        dk, dv = kbufs[d], vbufs[d]
+        with torch.cuda.stream(s):
+            dk.copy_(hk, non_blocking=True)
+            dv.copy_(hv, non_blocking=True)
+            R.radsort_sort(ctypes.c_void_p(dk.data_ptr()), ctypes.c_void_p(dv.data_ptr()), n, kb, db,
+                           ctypes.c_void_p(s.cuda_stream))
+            outs[d][0].copy_(dk, non_blocking=True)
+            outs[d][1].copy_(dv, non_blocking=True)
 
-    step()
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
-    barrier()
-    ms = e0.elapsed_time(e1) / steps
-    R.radsort_device_status()
+    def timed(ss, steps):
+        for i in range(len(ss)):  # untimed: one step per stream
+            step(ss[i], i)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in ss:
+            s.wait_stream(stream)
+        for i in range(steps):
+            step(ss[i % len(ss)], i % len(ss))
+        for s in ss:
+            stream.wait_stream(s)
+        e1.record(stream)
+        barrier()
+        R.radsort_device_status()
+        return e0.elapsed_time(e1) / steps
+
+    steps = max(2 * depth, min(a.steps, 12))
+    ms_serial = timed([stream], max(2, min(a.steps, 5)))
+    ms = timed(streams, steps)
+    # the last step's result, checked on the host: sorted, and a permutation
+    # of the input that keeps equal keys in input order
+    k = outs[(steps - 1) % depth][0].numpy()
+    k = k.view(np.uint32) if kb == 4 else k.view(np.uint64)
+    v = outs[(steps - 1) % depth][1].numpy().astype(np.int64)
+    src = hk.numpy().view(k.dtype)
+    eq = k[1:] == k[:-1]
+    if not (np.all(k[1:] >= k[:-1]) and np.array_equal(src[v], k) and np.all(v[1:][eq] > v[:-1][eq])):
+        raise SystemExit("bench: end-to-end result is wrong")
     return {"value": world * n / (ms / 1e3) / 1e9, "unit": "Gkeys/s",
             "h2d_bytes_per_step": n * E, "d2h_bytes_per_step": n * E, "steps": steps,
-            "call": "radsort_sort (automatic plan, allocating, stream-ordered) with pinned host buffers"}
+            "streams": depth, "ms_per_step": round(ms, 3),
+            "serial": {"value": round(world * n / (ms_serial / 1e3) / 1e9, 3), "ms_per_step": round(ms_serial, 3),
+                       "streams": 1},
+            "call": "radsort_sort (automatic plan, allocating, stream-ordered) with pinned host buffers; "
+                    "H2D, sort and D2H of each step on one of `streams` streams, steps overlapped"}
 
 
 def run_segmented(a):
@@ -500,7 +537,7 @@ def main():
     # ---- end to end through the public call with host buffers
     e2e = None
     if not a.no_e2e:
-        e2e = end_to_end(a, R, keys0, vals0, kbufs[0], vbufs[0], n, kb, db, E, world, barrier, stream)
+        e2e = end_to_end(a, R, keys0, vals0, kbufs, vbufs, n, kb, db, E, world, barrier, stream)
 
     # ---- out-of-place comparator on the same data and GPU
     oop = None
