@@ -218,21 +218,6 @@ def replica_result(ms, n, steps, world, dist, device):
     return ms_max, world * steps * n / (ms_max / 1e3) / 1e9
 
 
-def oop_scratch_bytes(n, kb, db):
-    """Scratch of the out-of-place comparator besides its alternate arrays:
-    digit histograms and offsets, and the look-back ring (R tiles x sigma
-    64-bit words plus R done tags), as the library sizes them."""
-    sigma = 1 << db
-    nt = -(-8 * kb // db)
-    tile = {(4, 8): 8192, (4, 11): 4096, (8, 8): 4096, (8, 11): 2048}[(kb, db)]
-    ntiles = -(-n // tile)
-    rows = 1
-    while rows < ntiles and rows < (4096 if sigma <= 256 else 1024):
-        rows <<= 1
-    al = lambda x: (x + 255) // 256 * 256
-    return al(nt * sigma * 4) + al(nt * (sigma + 1) * 4) + al(rows * sigma * 8 + rows * 4) + al(256)
-
-
 def end_to_end(a, R, keys0, vals0, kbufs, vbufs, n, kb, db, E, world, barrier, stream):
     """Same metric through the public call radsort_sort with pinned host
     buffers.  Every step copies its inputs host -> device, sorts them with
@@ -512,9 +497,15 @@ def main():
 
     # ---- the paper's chunk layout (Sec. 4.3), one chunk per SM, same data
     plan2 = None
+    ws2 = None
     if not a.no_oop and lay != "chunks":
         b2, p2 = 256, sms
-        ws2 = R.radsort_workspace_size(n, kb, 4, db, b2, p2, "chunks")
+        try:
+            ws2 = R.radsort_workspace_size(n, kb, 4, db, b2, p2, "chunks")
+        except R.RadsortError as err:  # e.g. chain sequence numbers overflow (sigma = 2048, 2^30)
+            plan2 = {"layout": "chunks", "block_size": b2, "num_chunks": p2,
+                     "unavailable": f"radsort_workspace_size: {err}"}
+    if ws2 is not None:
         wst = torch.empty(max(ws2, 1), dtype=torch.uint8, device=dev)
         for i in range(min(nbuf, 2)):
             refill(i)
@@ -566,7 +557,7 @@ def main():
         oval = world * a.steps * n / (oms / 1e3) / 1e9
         oop = {"value": round(oval, 3), "unit": "Gkeys/s", "ms_per_step": oms / a.steps,
                # the alternate arrays plus histograms and the look-back ring
-               "extra_bytes": n * E + oop_scratch_bytes(n, kb, db),
+               "extra_bytes": n * E + R.radsort_lsd_oop_scratch_size(n, kb, 4, db),
                "radsort_over_oop": round(value / oval, 4)}
         del ka, va
 

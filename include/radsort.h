@@ -151,6 +151,15 @@ radsort_status radsort_lsd_oop_sort(void *keys, uint32_t *values, void *keys_alt
                                     void *stream);
 
 /*
+ * Device scratch that radsort_lsd_oop_sort allocates (stream-ordered) and
+ * frees within the call, besides the caller's alternate arrays: the digit
+ * histograms and bucket offsets of every round, and the look-back ring.
+ * value_bytes: 0 (keys only) or 4.  Host-only; EINVAL on a bad width.
+ */
+radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_bytes,
+                                            int digit_bits, size_t *bytes);
+
+/*
  * Batched segmented sort: each segment [offsets[s], offsets[s+1]) of keys (and
  * values) is sorted stably and independently (n = offsets[num_segments]).
  * offsets_dev is the device copy of the num_segments+1 offsets (read by the

@@ -876,6 +876,16 @@ radsort_status radsort_lsd_oop_sort(void *keys, uint32_t *values, void *keys_alt
         launch_lsd_oop(keys, values, keys_alt, values_alt, n, key_bytes, digit_bits, as_stream(stream)));
 }
 
+radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_bytes,
+                                            int digit_bits, size_t *bytes)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11) ||
+        (value_bytes != 0 && value_bytes != 4) || !bytes)
+        return RADSORT_EINVAL;
+    *bytes = n <= 1 ? 0 : lsd_oop_scratch_bytes(n, key_bytes, digit_bits, value_bytes == 4);
+    return RADSORT_OK;
+}
+
 radsort_status radsort_device_status(void *stream)
 {
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));

@@ -502,11 +502,16 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     // per bucket: tcnt, bstart, gpos, O (sigma + 1); with SMALL, Radsort adds
     // the tables ns0, ns1, sh
     static constexpr int NBK = (!OOP && SMALL) ? 7 : 4;
-    static constexpr size_t o_qb = o_bk + al((size_t(NBK) * SIGMA + 4) * 4);
     // touched blocks per tile: at most TILE/b + 2 per bucket with elements
     static constexpr int LIST = MAXM + 2 * (SIGMA < TILE ? SIGMA : TILE) + 2;
-    static constexpr size_t o_lk = o_qb + al(size_t(SIGMA) * 8);
-    static constexpr size_t o_meta = o_lk + (OOP ? 0 : al(size_t(LIST) * (SMALL ? 8 : 4)));
+    static constexpr size_t QB_BYTES = al(size_t(SIGMA) * 8);
+    static constexpr size_t LK_BYTES = OOP ? 0 : al(size_t(LIST) * (SMALL ? 8 : 4));
+    // sigma = 2048: the per-bucket run offsets and the block list live in
+    // the warp-row region, which the tile no longer needs once reordered
+    static constexpr bool ALIAS = !SMALL && QB_BYTES + LK_BYTES <= size_t(NW) * HROW * 2;
+    static constexpr size_t o_qb = ALIAS ? o_hist : o_bk + al((size_t(NBK) * SIGMA + 4) * 4);
+    static constexpr size_t o_lk = o_qb + QB_BYTES;
+    static constexpr size_t o_meta = ALIAS ? o_bk + al((size_t(NBK) * SIGMA + 4) * 4) : o_lk + LK_BYTES;
     static constexpr size_t o_bar = o_meta + al(STAGES * 16);
     static constexpr size_t o_misc = o_bar + al(2 * STAGES * 8);
     static constexpr size_t SMEM = o_misc + 512;
@@ -894,22 +899,32 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 __syncwarp();
             }
         } else {
-            unsigned peers[C::ITEMS];
-#pragma unroll
-            for (int it = 0; it < C::ITEMS; ++it)
-                peers[it] = peer_mask<DB>(dig(it), dig(it) < SIGMA);
+            // a few rows at a time: their peer masks (independent ballots),
+            // then row by row the lowest lane of each digit group reads and
+            // advances the running count and passes the old count to its
+            // group with a shuffle
+            constexpr int CH = C::ITEMS % 4 == 0 ? 4 : (C::ITEMS % 2 == 0 ? 2 : 1);
             __syncwarp();
 #pragma unroll
-            for (int it = 0; it < C::ITEMS; ++it) {
-                const uint32_t d = dig(it);
-                uint32_t base = 0;
-                if (d < SIGMA)
-                    base = hw[d];
-                set_rk(it, base + __popc(peers[it] & lt));
-                __syncwarp();
-                if (d < SIGMA && (__ffs(peers[it]) - 1) == lane)
-                    hw[d] = static_cast<uint16_t>(base + __popc(peers[it]));
-                __syncwarp();
+            for (int i0 = 0; i0 < C::ITEMS; i0 += CH) {
+                unsigned peers[CH];
+#pragma unroll
+                for (int q = 0; q < CH; ++q)
+                    peers[q] = peer_mask<DB>(dig(i0 + q), dig(i0 + q) < SIGMA);
+#pragma unroll
+                for (int q = 0; q < CH; ++q) {
+                    const uint32_t d = dig(i0 + q);
+                    const unsigned pm = peers[q];
+                    const int ld = pm ? __ffs(pm) - 1 : lane;
+                    uint32_t base = 0;
+                    if (d < SIGMA && ld == lane) {
+                        base = hw[d];
+                        hw[d] = static_cast<uint16_t>(base + __popc(pm));
+                    }
+                    base = __shfl_sync(0xffffffffu, base, ld);
+                    set_rk(i0 + q, base + __popc(pm & lt));
+                    __syncwarp();
+                }
             }
         }
         bar();
@@ -981,6 +996,9 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 }
             }
         }
+
+        if constexpr (C::ALIAS)
+            bar(); // every warp has read its row before qb and the list overwrite it
 
         // ---- 4. global offset of each bucket's run (look-back); Radsort:
         // blocks touched, blocks taken here and by earlier tiles, list slots
@@ -1192,21 +1210,22 @@ static int lb_ctas(size_t ntiles)
 template <typename F> static cudaError_t lb_dispatch(int kb, int db, bool hasv, F &&f)
 {
     using u64 = unsigned long long;
-    // 8-bit digits: the largest tiles that two stages and the tables leave
-    // room for (per-tile costs scale with sigma, not with the tile), each a
-    // multiple of 2048 so that blocks of up to 2048 elements fit whole
+    // The largest tiles that two stages and the tables leave room for
+    // (per-tile costs scale with sigma, not with the tile), each a multiple
+    // of 2048 so that blocks of up to 2048 elements fit whole; 11-bit digits
+    // keep their run offsets and block list in the warp rows (ALIAS)
     if (kb == 4) {
         if (db == 8)
             return hasv ? f.template operator()<uint32_t, true, 8, 10240, 16, 2>()
                         : f.template operator()<uint32_t, false, 8, 16384, 16, 2>();
-        return hasv ? f.template operator()<uint32_t, true, 11, 4096, 8, 2>()
-                    : f.template operator()<uint32_t, false, 11, 4096, 8, 3>();
+        return hasv ? f.template operator()<uint32_t, true, 11, 8192, 16, 2>()
+                    : f.template operator()<uint32_t, false, 11, 16384, 16, 2>();
     }
     if (db == 8)
         return hasv ? f.template operator()<u64, true, 8, 6144, 16, 2>()
                     : f.template operator()<u64, false, 8, 10240, 16, 2>();
-    return hasv ? f.template operator()<u64, true, 11, 2048, 8, 3>()
-                : f.template operator()<u64, false, 11, 4096, 8, 2>();
+    return hasv ? f.template operator()<u64, true, 11, 4096, 16, 2>()
+                : f.template operator()<u64, false, 11, 8192, 16, 2>();
 }
 
 } // namespace

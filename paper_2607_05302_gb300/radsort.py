@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
             "radsort_sort_ex": ([vp, vp, sz, i, i, u32, pplan, vp, sz, vp], i),
             "radsort_sort_rounds": ([vp, vp, sz, i, i, i, pplan, vp, vp, vp], i),
             "radsort_lsd_oop_sort": ([vp, vp, vp, vp, sz, i, i, vp], i),
+            "radsort_lsd_oop_scratch_size": ([sz, i, i, i, ctypes.POINTER(sz)], i),
             "radsort_float_keys": ([vp, sz, i, vp], i),
             "radsort_device_status": ([vp], i),
             "radsort_trace_enable": ([i], i),
@@ -84,7 +85,8 @@ def lib() -> ctypes.CDLL:
 # exported names declared in include/radsort.h
 EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_workspace_size", "radsort_sort",
            "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_sort_segmented",
-           "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort", "radsort_float_keys",
+           "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
+           "radsort_lsd_oop_scratch_size", "radsort_float_keys",
            "radsort_device_status", "radsort_trace_enable", "radsort_trace_read",
            "radsort_launch_count")
 
@@ -149,6 +151,13 @@ def radsort_sort_rounds(keys, values, n, key_bytes, digit_bits, rounds, out_keys
                                   _plan(block_size, num_chunks, layout), out_keys, out_values,
                                   stream),
         "radsort_sort_rounds")
+
+
+def radsort_lsd_oop_scratch_size(n, key_bytes, value_bytes, digit_bits):
+    out = ctypes.c_size_t(0)
+    _ok(lib().radsort_lsd_oop_scratch_size(n, key_bytes, value_bytes, digit_bits, ctypes.byref(out)),
+        "radsort_lsd_oop_scratch_size")
+    return out.value
 
 
 def radsort_lsd_oop_sort(keys, values, keys_alt, values_alt, n, key_bytes, digit_bits, stream):

@@ -91,3 +91,27 @@ def test_plan_layouts_by_size(lib):
     # the scratch workspace holds the alternate keys and values
     assert R.radsort_workspace_size(n, 4, 4, 8) >= n * 8
     assert R.radsort_workspace_size(n, 4, 4, 8, layout="grid") < R.radsort_workspace_size(n, 4, 4, 8) + (16 << 20)
+
+
+def test_comparator_scratch_size(lib):
+    """Alg. 1's comparator needs, besides its n-element alternate arrays, the
+    histograms and offsets of every digit position (n_t x sigma words each)
+    and a look-back ring of at most 4096 (sigma = 256) or 1024 (sigma = 2048)
+    rows of sigma 64-bit words: bounded whatever n."""
+    from paper_2607_05302_gb300 import radsort as R
+
+    assert R.radsort_lsd_oop_scratch_size(1, 4, 4, 8) == 0
+    for kb, db in ((4, 8), (4, 11), (8, 8), (8, 11)):
+        sigma, nt = 1 << db, -(-8 * kb // db)
+        tables = nt * sigma * 4 + nt * (sigma + 1) * 4
+        cap = (4096 if db == 8 else 1024) * (sigma * 8 + 4)
+        prev = 0
+        for n in (1000, 1 << 20, 1 << 26, 1 << 30):
+            s = R.radsort_lsd_oop_scratch_size(n, kb, 4, db)
+            assert tables + sigma * 8 <= s <= tables + cap + 4096
+            assert s >= prev
+            prev = s
+        assert s <= 0.02 * (1 << 30) * (kb + 4)
+    bad = ctypes.c_size_t(0)
+    assert lib.radsort_lsd_oop_scratch_size(100, 4, 2, 8, ctypes.byref(bad)) == R.RADSORT_EINVAL
+    assert lib.radsort_lsd_oop_scratch_size(100, 4, 4, 9, ctypes.byref(bad)) == R.RADSORT_EINVAL
