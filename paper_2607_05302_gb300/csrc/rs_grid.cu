@@ -498,7 +498,7 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     static constexpr size_t o_stage = 0;
     static constexpr size_t o_hist = o_stage + STAGES * STAGE;
     static constexpr size_t o_tab = o_hist + al(size_t(NW) * HROW * 2);
-    static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * SIGMA * 4) : 0);
+    static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * 2 * SIGMA * 4) : 0);
     // per bucket: tcnt, bstart, gpos, O (sigma + 1); with SMALL, Radsort adds
     // the tables ns0, ns1, sh
     static constexpr int NBK = (!OOP && SMALL) ? 7 : 4;
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             stab[c] = a.tab[SIGMA + 1 + c];
     }
     if constexpr (C::PTAB)
-        for (int i = tid; i < NW * SIGMA; i += C::THREADS)
+        for (int i = tid; i < 2 * NW * SIGMA; i += C::THREADS)
             ptab[i] = 0u;
     __syncthreads();
 
@@ -878,11 +878,14 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             // row by row: lanes with the same digit OR their bit into the
             // digit's mask word, read back the mask and the warp's running
             // count; the lowest of those lanes advances the count and clears
-            // the word (the mask table is all zero between rows)
-            unsigned *pt = ptab + warp * SIGMA;
+            // the word.  Rows alternate between two mask tables, so the
+            // clearing of one row and the ORs of the next never meet (a
+            // table is all zero again two rows later)
+            unsigned *pt0 = ptab + warp * 2 * SIGMA;
             __syncwarp();
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it) {
+                unsigned *pt = pt0 + (it & 1) * SIGMA;
                 const uint32_t d = dig(it);
                 const bool v = d < SIGMA;
                 if (v)
@@ -896,8 +899,8 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                     hw[d] = static_cast<uint16_t>(base + __popc(pm));
                     pt[d] = 0u;
                 }
-                __syncwarp();
             }
+            __syncwarp();
         } else {
             // a few rows at a time: their peer masks (independent ballots),
             // then row by row the lowest lane of each digit group reads and
