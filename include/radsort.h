@@ -220,6 +220,17 @@ radsort_status radsort_float_keys(uint32_t *keys, size_t n, int inverse, void *s
 radsort_status radsort_device_status(void *stream);
 
 /*
+ * Failure-path probe (no counterpart in the paper; for tests).  Launches one
+ * thread on `stream` that waits for the device word *flag to become non-zero
+ * the way every wait of the library does: at most `iterations` polls, each
+ * followed by a sleep of at least 64 ns (1 <= iterations <= 2^26, the
+ * library's own limit).  If the flag stays 0 the wait runs out, and the next
+ * radsort_device_status returns RADSORT_ETIMEOUT; the context stays usable.
+ * EINVAL (synchronously) on a null flag or an iteration count out of range.
+ */
+radsort_status radsort_debug_wait_probe(const uint32_t *flag, unsigned iterations, void *stream);
+
+/*
  * Tracing (no counterpart in the paper; measurement support).  While enabled,
  * every sort records a CUDA event pair on its own stream around each phase:
  * setup (Alg. 4), each round's sortPhase kernel (Alg. 5), each fixupPhase

@@ -13,6 +13,12 @@
 #include "rs_kernels.cuh"
 
 namespace rs {
+// the failure-path probe (csrc/rs_finalize.cu)
+cudaError_t launch_wait_probe(const uint32_t *flag, unsigned limit, cudaStream_t st);
+unsigned wait_spin_limit();
+} // namespace rs
+
+namespace rs {
 
 std::atomic<unsigned long long> g_launches{0};
 
@@ -884,6 +890,13 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
         return RADSORT_EINVAL;
     *bytes = n <= 1 ? 0 : lsd_oop_scratch_bytes(n, key_bytes, digit_bits, value_bytes == 4);
     return RADSORT_OK;
+}
+
+radsort_status radsort_debug_wait_probe(const uint32_t *flag, unsigned iterations, void *stream)
+{
+    if (!flag || iterations == 0 || iterations > wait_spin_limit())
+        return RADSORT_EINVAL;
+    return cuda_status(launch_wait_probe(flag, iterations, as_stream(stream)));
 }
 
 radsort_status radsort_device_status(void *stream)

@@ -125,9 +125,9 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // bounded wait until *p != 0
-__device__ __forceinline__ bool wait_flag(const uint32_t *p)
+__device__ __forceinline__ bool wait_flag(const uint32_t *p, unsigned limit = SPIN_LIMIT)
 {
-    for (unsigned it = 0; it < SPIN_LIMIT; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         if (ld_acquire(p))
             return true;
         if ((it & 1023u) == 1023u && wait_failed())
@@ -975,6 +975,24 @@ __global__ void k_float_keys(uint32_t *u, size_t n, int inverse)
         u[i] = inverse ? (x ^ (top ? 0x80000000u : 0xFFFFFFFFu))
                        : (x ^ (top ? 0xFFFFFFFFu : 0x80000000u));
     }
+}
+
+// One thread waits for *flag like the stride and slot waits above, with at
+// most `limit` polls; a flag that stays 0 makes the wait run out and records
+// ST_TIMEOUT (the failure path, exercised without a fault or a hang)
+__global__ void k_wait_probe(const uint32_t *flag, unsigned limit)
+{
+    if (threadIdx.x == 0)
+        (void)wait_flag(flag, limit);
+}
+
+unsigned wait_spin_limit() { return SPIN_LIMIT; }
+
+cudaError_t launch_wait_probe(const uint32_t *flag, unsigned limit, cudaStream_t st)
+{
+    k_wait_probe<<<1, 32, 0, st>>>(flag, limit);
+    g_launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_float_keys(uint32_t *keys, size_t n, int inverse, cudaStream_t st)

@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
             "radsort_lsd_oop_scratch_size": ([sz, i, i, i, ctypes.POINTER(sz)], i),
             "radsort_float_keys": ([vp, sz, i, vp], i),
             "radsort_device_status": ([vp], i),
+            "radsort_debug_wait_probe": ([vp, ctypes.c_uint, vp], i),
             "radsort_trace_enable": ([i], i),
             "radsort_trace_read": ([ctypes.POINTER(TraceRec), i, ctypes.POINTER(i)], i),
             "radsort_launch_count": ([ctypes.POINTER(ctypes.c_uint64)], i),
@@ -87,7 +88,7 @@ EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_workspace_size
            "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_sort_segmented",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
            "radsort_lsd_oop_scratch_size", "radsort_float_keys",
-           "radsort_device_status", "radsort_trace_enable", "radsort_trace_read",
+           "radsort_device_status", "radsort_debug_wait_probe", "radsort_trace_enable", "radsort_trace_read",
            "radsort_launch_count")
 
 
@@ -171,6 +172,13 @@ def radsort_float_keys(keys, n, inverse, stream):
 
 def radsort_device_status(stream=None):
     _ok(lib().radsort_device_status(stream), "device status")
+
+
+def radsort_debug_wait_probe(flag, iterations, stream=None):
+    """One bounded wait on the device word `flag` (a CUDA int32 tensor); a
+    flag that stays 0 makes the next radsort_device_status raise ETIMEOUT."""
+    _ok(lib().radsort_debug_wait_probe(_ptr(flag), iterations, _torch_stream(stream)),
+        "radsort_debug_wait_probe")
 
 
 def radsort_trace_enable(on: bool):

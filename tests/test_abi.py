@@ -115,3 +115,14 @@ def test_comparator_scratch_size(lib):
     bad = ctypes.c_size_t(0)
     assert lib.radsort_lsd_oop_scratch_size(100, 4, 2, 8, ctypes.byref(bad)) == R.RADSORT_EINVAL
     assert lib.radsort_lsd_oop_scratch_size(100, 4, 4, 9, ctypes.byref(bad)) == R.RADSORT_EINVAL
+
+
+def test_wait_probe_argument_errors(lib):
+    """The failure-path probe rejects a null flag and iteration counts outside
+    1 .. 2^26 (the library's own wait limit) before launching anything."""
+    from paper_2607_05302_gb300 import radsort as R
+
+    flag = ctypes.c_void_p(256)
+    assert lib.radsort_debug_wait_probe(None, 100, None) == R.RADSORT_EINVAL
+    assert lib.radsort_debug_wait_probe(flag, 0, None) == R.RADSORT_EINVAL
+    assert lib.radsort_debug_wait_probe(flag, (1 << 26) + 1, None) == R.RADSORT_EINVAL
