@@ -170,28 +170,36 @@ __global__ void k_fz_edges(FinArgs a)
 // mode 0: val = minimum position of the window; mode 1: val = window length.
 // Each thread only rewrites its own entry, and any neighbour value it reads
 // is a valid window, so asynchronous updates only speed convergence.
+constexpr int JUMP_STEPS = 3;
+
 __global__ void k_fz_jump(unsigned long long *jump, uint32_t npi, int mode, uint32_t *changes,
                           int round)
 {
     // once a round changed nothing the entries are final: later rounds exit
     if (round > 0 && *(volatile uint32_t *)&changes[round - 1] == 0)
         return;
+    // JUMP_STEPS steps per launch: every entry always describes a valid
+    // window (its end and the min / sum over it), so an entry read while its
+    // owner updates it is a valid window too, and each step adds at least the
+    // window every entry had when the launch began: windows grow at least
+    // (JUMP_STEPS + 1)-fold per launch
     bool changed = false;
-    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npi; x += gridDim.x * blockDim.x) {
-        const unsigned long long e = ld64(&jump[x]);
-        const uint32_t v = hi32(e);
-        if (v == ABS)
-            continue;
-        const unsigned long long f = ld64(&jump[lo32(e)]);
-        const uint32_t fv = hi32(f);
-        if (fv == ABS)
-            continue; // x's window already ends at an absorbing entry
-        const unsigned long long ne = pk(lo32(f), mode == 0 ? min(v, fv) : v + fv);
-        if (ne != e) {
-            st64(&jump[x], ne);
-            changed = true;
+    for (int step = 0; step < JUMP_STEPS; ++step)
+        for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npi; x += gridDim.x * blockDim.x) {
+            const unsigned long long e = ld64(&jump[x]);
+            const uint32_t v = hi32(e);
+            if (v == ABS)
+                continue;
+            const unsigned long long f = ld64(&jump[lo32(e)]);
+            const uint32_t fv = hi32(f);
+            if (fv == ABS)
+                continue; // x's window already ends at an absorbing entry
+            const unsigned long long ne = pk(lo32(f), mode == 0 ? min(v, fv) : v + fv);
+            if (ne != e) {
+                st64(&jump[x], ne);
+                changed = true;
+            }
         }
-    }
     if (__syncthreads_or(changed) && threadIdx.x == 0)
         atomicAdd(&changes[round], 1u);
 }
@@ -900,8 +908,10 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
         grid = sms * 8;
     if (grid < 1)
         grid = 1;
+    // launches until every window reaches n_pi (growth (JUMP_STEPS+1)-fold
+    // each), plus one that sees no change
     int rounds = 1;
-    while ((1u << rounds) < g.npi)
+    for (unsigned long long w = JUMP_STEPS + 1; w < g.npi; w *= JUMP_STEPS + 1)
         ++rounds;
     rounds += 1;
     k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
