@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -468,7 +469,7 @@ def main():
         refill(i)
     torch.cuda.synchronize()
 
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"), local)
+    clocks = Clocks(os.path.join(tempfile.gettempdir(), f"radsort_clocks_{os.getpid()}_rank{rank}.csv"), local)
     R.radsort_trace_read()  # drop warm-up records
     R.radsort_trace_enable(True)
     l0 = R.radsort_launch_count()
