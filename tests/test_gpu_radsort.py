@@ -243,3 +243,21 @@ def test_full_size_2p30_u64_properties(db):
     R.sort_tensors(kt, vals, digit_bits=db)
     R.radsort_device_status()
     check_sorted_stable_perm(r, kt, vals, 64)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+def test_u32_d11_look_back_ring_reused(dist):
+    """11-bit digits at n = 2^26 uint32 keys: 8192 tiles of keys + values and
+    4096 of keys alone, more than the look-back ring's 1024 rows, so ring
+    slots are reused within every round; with and without payloads."""
+    n = 1 << 26
+    keys = torch.from_numpy(W.make_keys(dist, n).view(np.int32)).to(DEV)
+    vals = torch.arange(n, dtype=torch.int32, device=DEV)
+    kt = keys.clone()
+    R.sort_tensors(kt, vals, digit_bits=11)
+    R.radsort_device_status()
+    check_sorted_stable_perm(keys, kt, vals, 32)
+    ko = keys.clone()
+    R.sort_tensors(ko, None, digit_bits=11)
+    R.radsort_device_status()
+    assert torch.equal(ko, kt)
