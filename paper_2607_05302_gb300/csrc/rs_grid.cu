@@ -548,7 +548,7 @@ template <int SIGMA>
 __device__ __forceinline__ uint32_t look_back(const unsigned long long *ring, uint32_t rmask,
                                               uint32_t tagbase, uint32_t t, int c)
 {
-    constexpr int LBW = 16;
+    constexpr int LBW = 8;
     uint32_t excl = 0;
     int x = static_cast<int>(t) - 1;
     unsigned spins = 0;
