@@ -475,8 +475,9 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     static_assert(THREADS <= 1024, "one CTA holds at most 1024 threads");
     // threads per bucket in the column passes (each sums NW / TPB warp rows):
     // measured with 16 warps, one thread per bucket is fastest for sigma =
-    // 256 (round 1.86 -> 1.83 ms at 2^28), two for sigma = 2048
-    static constexpr int TPB = NW >= 16 ? (DB <= 8 ? 1 : 2) : (NW >= 4 ? 2 : 1);
+    // 256 (round 1.86 -> 1.83 ms at 2^28); for sigma = 2048 two were 5%
+    // faster at 2^26 but at 2^30 u64 left some rounds 3x slower, four do not
+    static constexpr int TPB = NW >= 16 ? (DB <= 8 ? 1 : 4) : (NW >= 4 ? 2 : 1);
     static_assert(NW % TPB == 0, "rows split evenly");
     // more than 16 elements per thread: digits are recomputed from the keys
     // and warp ranks kept as 16-bit halves, to stay within the registers
