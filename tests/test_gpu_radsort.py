@@ -261,3 +261,40 @@ def test_u32_d11_look_back_ring_reused(dist):
     R.sort_tensors(ko, None, digit_bits=11)
     R.radsort_device_status()
     assert torch.equal(ko, kt)
+
+
+def _check_large(orig, kt, vals):
+    """Sorted (unsigned), payload a permutation with keys[i] = orig[payload[i]],
+    equal keys in payload order: chunked to bound the temporaries."""
+    n = kt.numel()
+    v = vals.to(torch.int64) & 0xFFFFFFFF
+    seen = torch.zeros(n, dtype=torch.bool, device=DEV)
+    seen[v] = True
+    assert bool(seen.all())
+    del seen
+    step = 1 << 28
+    for s in range(0, n, step):
+        e = min(n, s + step + 1)
+        k = kt[s:e].to(torch.int64) & 0xFFFFFFFF
+        assert bool((k[1:] >= k[:-1]).all())
+        assert torch.equal(orig[v[s:e]], kt[s:e])
+        eq = k[1:] == k[:-1]
+        vv = v[s:e]
+        assert bool((vv[1:][eq] > vv[:-1][eq]).all())
+
+
+@pytest.mark.parametrize("n,plan", [((1 << 31) + 12345, "auto"), ((1 << 31) - 1, "grid")])
+def test_largest_sizes(n, plan):
+    """The largest arrays each layout takes: past 2^31 elements the automatic
+    plan is the chunk layout (64-bit element positions); the grid layout takes
+    up to 2^31 - 1 (31-bit look-back prefixes).  uint32 keys + index payload,
+    16 GiB of data."""
+    r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=DEV)
+    keys = ((r >> 32) & 0xFFFFFFFF).to(torch.int64).to(torch.int32)
+    del r
+    # payload = index as uint32 (int32 bits wrap past 2^31 - 1)
+    vals = torch.arange(n, dtype=torch.int64, device=DEV).to(torch.int32)
+    kt = keys.clone()
+    R.sort_tensors(kt, vals, layout=plan)
+    R.radsort_device_status()
+    _check_large(keys, kt, vals)
