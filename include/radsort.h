@@ -94,6 +94,24 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
                                     radsort_plan *plan);
 
 /*
+ * Autotuner (no counterpart in the paper): times, on `stream`, sorts of a copy
+ * of keys[0..n) (and values, if not NULL) under every plan of the automatic
+ * plan's layout whose workspace fits the same budget (2% of the arrays, or
+ * 1.25x the least workspace of any block size), and returns the fastest in
+ * *plan.  Grid layout: block sizes 256 .. 4096 that a tile holds whole; chunk
+ * layout: the automatic chunk count with block sizes 256 .. 2048.  Arrays up
+ * to RADSORT_SCRATCH_MAX_N get the out-of-place plan without timing.
+ * keys and values are read, never written (each timed sort starts from a
+ * fresh device copy); while tuning, the call allocates that copy and the
+ * largest candidate workspace (stream-ordered) and waits for the stream.
+ * Results are cached per (ceil(log2 n), key_bytes, value bytes, digit_bits):
+ * a cached entry returns without touching the GPU.  EINVAL on a bad width,
+ * a NULL plan or an unaligned array; a failed timed sort returns its status.
+ */
+radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t n, int key_bytes,
+                                int digit_bits, void *stream, radsort_plan *plan);
+
+/*
  * Bytes of device workspace radsort_sort_ex needs: the scratch array T
  * (2*sigma*p blocks in the chunk layout, Sec. 2.1 and 4.3; 4*sigma + 1 in the
  * grid layout), the block permutation pi and its successor, the usage array

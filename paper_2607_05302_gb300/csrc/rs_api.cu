@@ -449,6 +449,79 @@ static cudaError_t run_rounds(const Geom &g, Bufs &w, int rounds, cudaStream_t s
 
 using namespace rs;
 
+// Workspace bytes of a plan (0 if the plan is not valid for these sizes).
+static size_t workspace_of(size_t n, int kb, int vb, int db, const radsort_plan &p)
+{
+    size_t bytes = 0;
+    return radsort_workspace_size(n, kb, vb, db, &p, &bytes) == RADSORT_OK ? bytes : 0;
+}
+
+namespace {
+// autotuner cache: (ceil log2 n, key bytes, value bytes, digit bits) -> plan
+struct TuneEntry {
+    int lg, kb, vb, db;
+    radsort_plan plan;
+};
+constexpr int TUNE_CAP = 256;
+std::mutex g_tune_mu;
+TuneEntry g_tune[TUNE_CAP];
+int g_tune_n = 0;
+
+constexpr int MAX_CANDS = 8;
+struct Cands {
+    radsort_plan p[MAX_CANDS];
+    int n = 0;
+    void push_back(const radsort_plan &x)
+    {
+        if (n < MAX_CANDS)
+            p[n++] = x;
+    }
+    bool empty() const { return n == 0; }
+};
+
+// The candidate plans of the automatic plan's layout within its budget.
+Cands tune_candidates(size_t n, int kb, int vb, int db, const radsort_plan &base)
+{
+    Cands out;
+    const double two = 0.02 * double(n) * double(kb + vb);
+    if (base.layout == RADSORT_LAYOUT_GRID) {
+        const uint32_t cands[] = {256, 512, 1024, 2048, 4096};
+        size_t ws[5] = {}, least = 0;
+        for (int i = 0; i < 5; ++i) {
+            Geom g;
+            if (fill_geom_grid(n, kb, vb != 0, db, cands[i], &g) != RADSORT_OK)
+                continue;
+            ws[i] = layout(g, nullptr, nullptr);
+            if (!least || ws[i] < least)
+                least = ws[i];
+        }
+        const double budget = two > 1.25 * double(least) ? two : 1.25 * double(least);
+        for (int i = 0; i < 5; ++i)
+            if (ws[i] && double(ws[i]) <= budget) {
+                radsort_plan p{};
+                p.layout = RADSORT_LAYOUT_GRID;
+                p.block_size = cands[i];
+                p.num_chunks = 1;
+                out.push_back(p);
+            }
+    } else {
+        const double budget = two > double(workspace_of(n, kb, vb, db, base)) ? two
+                                                                           : double(workspace_of(n, kb, vb, db, base));
+        const uint32_t cands[] = {256, 512, 1024, 2048};
+        for (uint32_t b : cands) {
+            radsort_plan p = base;
+            p.block_size = b;
+            const size_t ws = workspace_of(n, kb, vb, db, p);
+            if (ws && double(ws) <= budget)
+                out.push_back(p);
+        }
+    }
+    if (out.empty())
+        out.push_back(base);
+    return out;
+}
+} // namespace
+
 extern "C" {
 
 const char *radsort_status_str(radsort_status s)
@@ -621,6 +694,109 @@ radsort_status radsort_sort_ex(void *keys, uint32_t *values, size_t n, int key_b
 {
     return sort_common(keys, values, n, key_bytes, digit_bits, flags, plan, workspace,
                        workspace_bytes, stream, -1, nullptr, nullptr);
+}
+
+
+radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t n, int key_bytes,
+                                int digit_bits, void *stream, radsort_plan *plan)
+{
+    if (!plan || (key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (n > 1 && (!keys || !aligned16(keys) || (values && !aligned16(values))))
+        return RADSORT_EINVAL;
+    const int vb = values ? 4 : 0;
+    radsort_plan base{};
+    radsort_status s = radsort_plan_default(n < 2 ? 2 : n, key_bytes, vb, digit_bits, &base);
+    if (s != RADSORT_OK)
+        return s;
+    if (n <= 1 || base.layout == RADSORT_LAYOUT_SCRATCH) {
+        *plan = base; // one out-of-place pass in the workspace: nothing to choose
+        return RADSORT_OK;
+    }
+    int lg = 0;
+    while ((size_t(1) << lg) < n)
+        ++lg;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (int i = 0; i < g_tune_n; ++i)
+            if (g_tune[i].lg == lg && g_tune[i].kb == key_bytes && g_tune[i].vb == vb &&
+                g_tune[i].db == digit_bits) {
+                *plan = g_tune[i].plan;
+                return RADSORT_OK;
+            }
+    }
+    const Cands cands = tune_candidates(n, key_bytes, vb, digit_bits, base);
+    size_t wsmax = 0;
+    for (int ci = 0; ci < cands.n; ++ci) {
+        const size_t ws = workspace_of(n, key_bytes, vb, digit_bits, cands.p[ci]);
+        wsmax = ws > wsmax ? ws : wsmax;
+    }
+    cudaStream_t st = as_stream(stream);
+    const size_t kbytes = align_up(n * key_bytes, 256), vbytes = values ? align_up(n * 4, 256) : 0;
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), kbytes + vbytes + wsmax, st);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    void *ck = buf;
+    uint32_t *cv = values ? reinterpret_cast<uint32_t *>(buf + kbytes) : nullptr;
+    void *ws = buf + kbytes + vbytes;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    radsort_plan best = base;
+    float best_ms = -1.f;
+    s = RADSORT_OK;
+    for (int ci = 0; ci < cands.n; ++ci) {
+        const radsort_plan &p = cands.p[ci];
+        float pm = -1.f;
+        for (int rep = 0; rep < 2 && s == RADSORT_OK; ++rep) {
+            e = cudaMemcpyAsync(ck, keys, n * key_bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess && values)
+                e = cudaMemcpyAsync(cv, values, n * 4, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess) {
+                s = cuda_status(e);
+                break;
+            }
+            s = radsort_sort_ex(ck, cv, n, key_bytes, digit_bits, 0, &p, ws, wsmax, stream);
+            if (s != RADSORT_OK)
+                break;
+            e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess)
+                e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                s = cuda_status(e);
+                break;
+            }
+            pm = pm < 0.f || ms < pm ? ms : pm;
+        }
+        if (s != RADSORT_OK)
+            break;
+        if (best_ms < 0.f || pm < best_ms) {
+            best_ms = pm;
+            best = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    if (s == RADSORT_OK)
+        s = radsort_device_status(stream); // a timed sort whose bounded wait ran out
+    if (s == RADSORT_OK && ef != cudaSuccess)
+        s = cuda_status(ef);
+    if (s != RADSORT_OK)
+        return s;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune_n < TUNE_CAP)
+            g_tune[g_tune_n++] = TuneEntry{lg, key_bytes, vb, digit_bits, best};
+    }
+    *plan = best;
+    return RADSORT_OK;
 }
 
 radsort_status radsort_sort(void *keys, uint32_t *values, size_t n, int key_bytes, int digit_bits,

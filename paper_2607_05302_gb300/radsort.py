@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
         sig = {
             "radsort_status_str": ([i], ctypes.c_char_p),
             "radsort_plan_default": ([sz, i, i, i, pplan], i),
+            "radsort_autotune": ([vp, vp, sz, i, i, vp, pplan], i),
             "radsort_workspace_size": ([sz, i, i, i, pplan, ctypes.POINTER(sz)], i),
             "radsort_sort": ([vp, vp, sz, i, i, vp], i),
             "radsort_sort_noalloc": ([vp, vp, sz, i, i, vp], i),
@@ -84,7 +85,7 @@ def lib() -> ctypes.CDLL:
 
 
 # exported names declared in include/radsort.h
-EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_workspace_size", "radsort_sort",
+EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_autotune", "radsort_workspace_size", "radsort_sort",
            "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_sort_segmented",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
            "radsort_lsd_oop_scratch_size", "radsort_float_keys",
@@ -122,6 +123,15 @@ def radsort_plan_default(n, key_bytes, value_bytes, digit_bits):
     p = Plan()
     _ok(lib().radsort_plan_default(n, key_bytes, value_bytes, digit_bits, ctypes.byref(p)),
         "radsort_plan_default")
+    return int(p.block_size), int(p.num_chunks), int(p.layout)
+
+
+def radsort_autotune(keys, values=None, *, digit_bits=8, stream=None):
+    """(block_size, num_chunks, layout) of the fastest plan for sorting these
+    CUDA tensors (timed on copies; the tensors are not modified)."""
+    p = Plan()
+    _ok(lib().radsort_autotune(_ptr(keys), _ptr(values), keys.numel(), _key_bytes(keys), digit_bits,
+                               _torch_stream(stream), ctypes.byref(p)), "radsort_autotune")
     return int(p.block_size), int(p.num_chunks), int(p.layout)
 
 

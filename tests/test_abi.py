@@ -126,3 +126,19 @@ def test_wait_probe_argument_errors(lib):
     assert lib.radsort_debug_wait_probe(None, 100, None) == R.RADSORT_EINVAL
     assert lib.radsort_debug_wait_probe(flag, 0, None) == R.RADSORT_EINVAL
     assert lib.radsort_debug_wait_probe(flag, (1 << 26) + 1, None) == R.RADSORT_EINVAL
+
+
+def test_autotune_without_timing(lib):
+    """The autotuner checks its arguments synchronously, and arrays up to
+    RADSORT_SCRATCH_MAX_N get the out-of-place plan without any GPU work."""
+    from paper_2607_05302_gb300 import radsort as R
+
+    p = R.Plan()
+    ptr = ctypes.c_void_p(256)
+    assert lib.radsort_autotune(ptr, None, 100, 4, 8, None, None) == R.RADSORT_EINVAL    # no plan
+    assert lib.radsort_autotune(ptr, None, 100, 3, 8, None, ctypes.byref(p)) == R.RADSORT_EINVAL
+    assert lib.radsort_autotune(ptr, None, 100, 4, 9, None, ctypes.byref(p)) == R.RADSORT_EINVAL
+    assert lib.radsort_autotune(ctypes.c_void_p(258), None, 100, 4, 8, None,
+                                ctypes.byref(p)) == R.RADSORT_EINVAL                      # alignment
+    assert lib.radsort_autotune(ptr, None, 1000, 4, 8, None, ctypes.byref(p)) == R.RADSORT_OK
+    assert p.layout == R.RADSORT_LAYOUT_SCRATCH

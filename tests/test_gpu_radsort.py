@@ -298,3 +298,28 @@ def test_largest_sizes(n, plan):
     R.sort_tensors(kt, vals, layout=plan)
     R.radsort_device_status()
     _check_large(keys, kt, vals)
+
+
+@pytest.mark.parametrize("kb,db", [(4, 8), (8, 11)])
+def test_autotune_plan_sorts_and_inputs_untouched(kb, db):
+    """radsort_autotune times every candidate plan on copies, leaves the
+    arrays as they were, returns a plan of the automatic plan's layout whose
+    sort matches the oracle, and answers a second call from its cache."""
+    import time
+
+    n = (1 << 21) + 77
+    keys = W.make_keys("uniform", n, 8 * kb)
+    vals = W.index_payload(n)
+    kt, vt = to_dev(keys), to_dev(vals)
+    b, p, lay = R.radsort_autotune(kt, vt, digit_bits=db)
+    R.radsort_device_status()
+    assert np.array_equal(from_dev(kt, keys.dtype), keys)
+    assert np.array_equal(from_dev(vt, np.uint32), vals)
+    assert lay == R.radsort_plan_default(n, kb, 4, db)[2]
+    assert R.radsort_workspace_size(n, kb, 4, db, b, p, lay) > 0
+    t0 = time.perf_counter()
+    assert R.radsort_autotune(kt, vt, digit_bits=db) == (b, p, lay)
+    assert time.perf_counter() - t0 < 0.05
+    gk, gv = gpu_sort(keys, vals, digit_bits=db, block_size=b, num_chunks=p, layout=lay)
+    ek, ev = oracle_sort(keys, vals, 8 * kb, db)
+    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
