@@ -105,7 +105,8 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
  * fresh device copy); while tuning, the call allocates that copy and the
  * largest candidate workspace (stream-ordered) and waits for the stream.
  * Results are cached per (ceil(log2 n), key_bytes, value bytes, digit_bits):
- * a cached entry returns without touching the GPU.  EINVAL on a bad width,
+ * a cached entry whose plan is valid for this n returns without touching the
+ * GPU (otherwise the call tunes again and replaces it).  EINVAL on a bad width,
  * a NULL plan or an unaligned array; a failed timed sort returns its status.
  */
 radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t n, int key_bytes,

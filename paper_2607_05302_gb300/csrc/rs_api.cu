@@ -717,10 +717,13 @@ radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t
     while ((size_t(1) << lg) < n)
         ++lg;
     {
+        // a cached plan is reused when it is valid for this n as well (the
+        // limits of a layout can fall inside a size class)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         for (int i = 0; i < g_tune_n; ++i)
             if (g_tune[i].lg == lg && g_tune[i].kb == key_bytes && g_tune[i].vb == vb &&
-                g_tune[i].db == digit_bits) {
+                g_tune[i].db == digit_bits && g_tune[i].plan.layout == base.layout &&
+                workspace_of(n, key_bytes, vb, digit_bits, g_tune[i].plan)) {
                 *plan = g_tune[i].plan;
                 return RADSORT_OK;
             }
@@ -792,8 +795,15 @@ radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t
         return s;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        if (g_tune_n < TUNE_CAP)
-            g_tune[g_tune_n++] = TuneEntry{lg, key_bytes, vb, digit_bits, best};
+        int slot = -1;
+        for (int i = 0; i < g_tune_n && slot < 0; ++i)
+            if (g_tune[i].lg == lg && g_tune[i].kb == key_bytes && g_tune[i].vb == vb &&
+                g_tune[i].db == digit_bits)
+                slot = i; // replaces an entry that did not fit this n
+        if (slot < 0 && g_tune_n < TUNE_CAP)
+            slot = g_tune_n++;
+        if (slot >= 0)
+            g_tune[slot] = TuneEntry{lg, key_bytes, vb, digit_bits, best};
     }
     *plan = best;
     return RADSORT_OK;
