@@ -142,3 +142,32 @@ def test_autotune_without_timing(lib):
                                 ctypes.byref(p)) == R.RADSORT_EINVAL                      # alignment
     assert lib.radsort_autotune(ptr, None, 1000, 4, 8, None, ctypes.byref(p)) == R.RADSORT_OK
     assert p.layout == R.RADSORT_LAYOUT_SCRATCH
+
+
+def test_segmented_workspace_size(lib):
+    """Host-side planning of radsort_sort_segmented: decreasing offsets are
+    rejected; the workspace covers the Radsort workspace of the longest
+    segment that takes the full path (above 2^18 elements, in the grid layout
+    at these sizes) plus a part that does not grow with the data; among
+    16-byte-aligned long segments the longest alone decides the long-segment
+    part; a long segment whose start is not 16-byte aligned is sorted out of
+    place and needs its alternate arrays."""
+    import numpy as np
+
+    from paper_2607_05302_gb300 import radsort as R
+
+    def ws(lens):
+        off = np.zeros(len(lens) + 1, np.uint64)
+        np.cumsum(np.array(lens, np.uint64), out=off[1:])
+        return R.segmented_workspace_size(off, 4, 4, 8)
+
+    with pytest.raises(R.RadsortError):
+        R.segmented_workspace_size(np.array([0, 10, 5], np.uint64), 4, 4, 8)
+    base = ws([100])
+    assert ws([100] * 1000) - base <= 1000 * 8 + 1024            # index words per segment
+    assert ws([5000] * 10) - ws([5000]) <= 10 * 8 + 1024          # medium segments: fixed buffers
+    big = (1 << 22) + 4
+    assert ws([big]) >= R.radsort_workspace_size(big, 4, 4, 8, layout="grid")
+    assert ws([big, 1 << 20, 300, 5000]) <= ws([big]) + 4 * 8 + 1024   # all starts aligned
+    odd = [3, 1 << 20]  # the long segment starts 12 bytes past an aligned address
+    assert ws(odd) >= base + (1 << 20) * 8
