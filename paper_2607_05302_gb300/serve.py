@@ -61,9 +61,9 @@ def footprint(req, method):
     E = req.key_bytes + 4
     if method == "radsort":
         return req.n * E + R.radsort_workspace_size(req.n, req.key_bytes, 4, 8)
-    # out of place: the second n-element buffer pair plus histograms and
-    # look-back status words
-    return 2 * req.n * E + req.n // 4 + (1 << 20)
+    # out of place: the array, the second n-element buffer pair, and the
+    # scratch the comparator allocates (histograms, offsets, look-back ring)
+    return 2 * req.n * E + R.radsort_lsd_oop_scratch_size(req.n, req.key_bytes, 4, 8)
 
 
 def _launch(req, method, stream, keep_result):

@@ -38,3 +38,32 @@ def test_distributions_shape():
     assert u64.dtype == np.uint64 and (u64 >> np.uint64(60)).max() == 15
     L = W.lognormal_lengths(20000)
     assert L.min() >= 16 and L.max() <= (1 << 22) and 3000 < np.median(L) < 5500
+
+
+def test_serving_footprints():
+    """Admission inputs of the serving loop, host-only: a Radsort request
+    holds its array plus its plan's workspace (within 2-3% from about 2^27
+    elements, where the O(sigma b) scratch and the look-back ring no longer
+    dominate; about 10% at 2^22),
+    an out-of-place one two arrays plus the comparator's scratch.  Above
+    RADSORT_SCRATCH_MAX_N elements Radsort's footprint is the smaller; up to
+    it the automatic plan is itself out of place in the workspace, and the two
+    are alike."""
+    from paper_2607_05302_gb300 import radsort as R
+    from paper_2607_05302_gb300 import serve as S
+
+    big = 0
+    for req in S.make_requests(400):
+        E = req.key_bytes + 4
+        r, o = S.footprint(req, "radsort"), S.footprint(req, "oop")
+        assert o >= 2 * req.n * E and r >= req.n * E
+        if req.n > R.RADSORT_SCRATCH_MAX_N:
+            big += 1
+            assert r < o
+        else:
+            assert r <= 1.1 * o
+        if req.n >= 1 << 27:
+            assert r <= 1.03 * req.n * E
+        elif req.n >= 1 << 22:
+            assert r <= 1.12 * req.n * E
+    assert big > 100
