@@ -171,3 +171,23 @@ def test_segmented_workspace_size(lib):
     assert ws([big, 1 << 20, 300, 5000]) <= ws([big]) + 4 * 8 + 1024   # all starts aligned
     odd = [3, 1 << 20]  # the long segment starts 12 bytes past an aligned address
     assert ws(odd) >= base + (1 << 20) * 8
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Every function include/radsort.h declares is bound in radsort.py with
+    as many arguments as the header gives it (a missing or extra argument
+    would be read as garbage by the library)."""
+    from paper_2607_05302_gb300 import radsort as R
+
+    txt = "\n".join(open(os.path.join(ROOT, "include", h)).read()
+                    for h in os.listdir(os.path.join(ROOT, "include")) if h.endswith(".h"))
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    decls = dict(re.findall(r"\b(radsort_\w+)\s*\(([^)]*)\)\s*;", txt))
+    assert set(decls) == set(header_functions())
+    for name, params in decls.items():
+        p = params.strip()
+        nargs = 0 if p in ("", "void") else p.count(",") + 1
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == nargs, (name, len(fn.argtypes), nargs)
+    assert set(R.EXPORTS) == set(decls)
