@@ -101,6 +101,27 @@ def oracle_sample_rate(a, seconds):
     return reps * m / el / 1e9, f"{reps} x oracle Radsort (p=1, b=1024) of 2^{m.bit_length() - 1} keys of the same distribution", el
 
 
+def host_cpu():
+    """The host CPU's name as the kernel reports it (x86: model name; Arm: the
+    implementer and part numbers), for the cpu_baseline records."""
+    import platform
+
+    info = {}
+    try:
+        for ln in open("/proc/cpuinfo"):
+            k, _, v = ln.partition(":")
+            k, v = k.strip(), v.strip()
+            if k and v and k not in info:
+                info[k] = v
+    except OSError:
+        pass
+    if "model name" in info:
+        return info["model name"]
+    if "CPU part" in info:
+        return f"{platform.machine()} implementer {info.get('CPU implementer', '?')} part {info['CPU part']}"
+    return platform.processor() or platform.machine()
+
+
 def run_reference(a, rank):
     if rank != 0:
         return
@@ -117,7 +138,7 @@ def run_reference(a, rank):
         "ms_per_step": 1e3 * sum(steps) / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32" if a.key_bytes == 4 else "u64", "data": "synthetic",
         "config": {"workload": workload_name(a), "n": 1 << a.log2n, "sample_n": m},
-        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                          "sample": f"each step: one oracle Radsort (single-threaded C, p=1, b=1024) of 2^{m.bit_length() - 1} keys of the same workload"},
         "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -586,7 +607,7 @@ def main():
     if rank == 0 and world == 1 and not a.no_cpu:
         rate, sample, el = oracle_sample_rate(a, a.cpu_seconds)
         cpu = {"value": rate, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": round(el, 2), "host_cores_available": os.cpu_count()}
+               "seconds": round(el, 2), "host_cores_available": os.cpu_count(), "cpu": host_cpu()}
 
     if rank == 0:
         line = {
