@@ -50,7 +50,7 @@ def prep(cnt, b):
     return O, shared, tab, n
 
 
-def replay(digits, sigma, b, tile, L=2, head=None):
+def replay(digits, sigma, b, tile, L=2, head=None, log=None):
     n = len(digits)
     cnt = np.bincount(digits, minlength=sigma)
     O, shared, tab, _ = prep(cnt, b)
@@ -86,6 +86,7 @@ def replay(digits, sigma, b, tile, L=2, head=None):
         kofs = np.concatenate([[0], np.cumsum(ks)])[:-1]
         fbase = nP + ans
         fcap = min(H + (t + 1) * M, H + n // b + 1)
+        took, touched = [], set()
         for c in range(sigma):
             ns0, ns1, fsh, lsh = tab[c]
             if ks[c]:
@@ -96,19 +97,25 @@ def replay(digits, sigma, b, tile, L=2, head=None):
                     assert j not in taken, "block taken twice"
                     assert idx < fcap, "Lemma 1"
                     taken[j] = idx
+                    took.append(j)
             if tc[c]:
                 for j in range(g[c] // b, (g[c] + tc[c] - 1) // b + 1):
                     assert j in taken, "block written before it was taken"
+                    touched.add(j)
         # stable placement of this tile's elements
         seen = np.zeros(sigma, dtype=np.int64)
         for i, dd in enumerate(d):
             out[g[dd] + seen[dd]] = lo + i
             seen[dd] += 1
         E += tc
+        if log is not None:
+            log.append((took, touched))
     assert sorted(taken) == list(range(NB))
     assert sorted(taken.values()) == list(range(NB))
     ref = np.argsort(digits, kind="stable")
     assert np.array_equal(out, ref)
+    if log is not None:
+        log.append(set(j for j, k in taken.items() if k < nP))  # taken before the round
     return nP
 
 
@@ -168,3 +175,73 @@ def test_head_start_of_l_plus_two_sigma_is_needed():
     replay(d, 8, 64, 64, L=1, head=3)
     with pytest.raises(AssertionError, match="Lemma 1"):
         replay(d, 8, 64, 64, L=1, head=2)
+
+
+def run_concurrent(digits, sigma, b, tile, L, ctas, seed):
+    """The same round with tiles on concurrent CTAs: a tile publishes its
+    counts, waits until every earlier tile has published (its look-back),
+    records the map entries of the blocks it takes, then waits for the map
+    entry of every other block it writes, as the kernel does.  Any schedule
+    ends (a tile only waits on earlier tiles) and every entry a tile waits for
+    is written by the round's preparation, an earlier tile or itself."""
+    import random
+
+    log = []
+    replay(digits, sigma, b, tile, L=L, log=log)
+    pre = log.pop()
+    ntiles = len(log)
+    rng = random.Random(seed)
+    published = [False] * ntiles
+    writer = {j: -1 for j in pre}  # block -> tile that recorded its entry
+    ticket = [0]
+
+    def cta():
+        while True:
+            t = ticket[0]
+            ticket[0] += 1
+            if t >= ntiles:
+                return
+            published[t] = True
+            yield
+            while not all(published[:t]):
+                yield
+            took, touched = log[t]
+            for j in took:
+                writer[j] = t
+                yield
+            for j in sorted(touched - set(took)):
+                while j not in writer:
+                    yield
+                assert writer[j] <= t
+            yield
+
+    actors = [cta() for _ in range(ctas)]
+    live = list(range(ctas))
+    steps = 0
+    while live:
+        i = rng.choice(live)
+        for _ in range(rng.choice((1, 3, 20, 100))):
+            try:
+                next(actors[i])
+            except StopIteration:
+                live.remove(i)
+                break
+            steps += 1
+        assert steps < 3_000_000, "no progress"
+    return writer
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("n,sigma,b,tile,kind", CASES[:4] + CASES[6:])
+def test_grid_round_on_concurrent_tiles(n, sigma, b, tile, kind, seed):
+    rng = np.random.default_rng(n * 7 + sigma)
+    if kind == "uniform":
+        d = rng.integers(0, sigma, n)
+    elif kind == "skew":
+        d = np.where(rng.random(n) < 0.9, 3 % sigma, rng.integers(0, sigma, n))
+    elif kind == "few":
+        d = rng.choice([0, 5, 7], n)
+    else:
+        d = np.sort(rng.integers(0, sigma, n))[::-1].copy()
+    writer = run_concurrent(d.astype(np.int64), sigma, b, tile, 2, 5, seed)
+    assert sorted(writer) == list(range(-(-n // b)))
