@@ -104,7 +104,8 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
  * keys and values are read, never written (each timed sort starts from a
  * fresh device copy); while tuning, the call allocates that copy and the
  * largest candidate workspace (stream-ordered) and waits for the stream.
- * Results are cached per (ceil(log2 n), key_bytes, value bytes, digit_bits):
+ * Results are cached per (device, ceil(log2 n), key_bytes, value bytes,
+ * digit_bits):
  * a cached entry whose plan is valid for this n returns without touching the
  * GPU (otherwise the call tunes again and replaces it).  EINVAL on a bad width,
  * a NULL plan or an unaligned array; a failed timed sort returns its status.
@@ -217,8 +218,10 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
  * one per SM) as fit; an n whose workspace does not fit even with one chunk
  * returns RADSORT_ENOMEM and enqueues nothing (up to about 1.07e9 elements
  * with 4-byte keys and values fit, 8.8e8 with 8-byte keys).
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
+ * Every call looks up the array's device address on the current device with
+ * cudaGetSymbolAddress (which allocates nothing), so the address stays right
+ * after a context reset; the first call on a device may also load the
+ * library's device code there, so make that first call before any stream
  * capture.  No call allocates or frees memory.  All calls share the one
  * array: calls that overlap on the GPU (other streams, other host threads)
  * race and corrupt each other; serialise them.  Each call rebuilds every

@@ -4,7 +4,6 @@
 // (Alg. 2).  Nothing here touches element data; every step runs in the
 // kernels of rs_round.cu and rs_finalize.cu.
 #include <atomic>
-#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -73,17 +72,30 @@ struct Scope {
 };
 } // namespace
 
+// SM count of the current device (cached per device ordinal)
 int num_sms()
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms <= 0)
-            sms = 152;
+    static std::atomic<int> cache[MAX_DEVICES] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
+        dev = -1;
+    if (dev >= 0) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0)
+            return c;
     }
+    int sms = 0;
+    if (dev < 0 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        return 152;
+    cache[dev].store(sms, std::memory_order_relaxed);
     return sms;
+}
+
+int current_device()
+{
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess ? dev : -1;
 }
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -96,12 +108,6 @@ static uint32_t ilog2(uint32_t x)
     while ((1u << r) < x)
         ++r;
     return r;
-}
-
-static long env_long(const char *name, long dflt)
-{
-    const char *s = std::getenv(name);
-    return s && *s ? std::strtol(s, nullptr, 10) : dflt;
 }
 
 static size_t layout(const Geom &g, void *base, Bufs *w);
@@ -185,9 +191,7 @@ static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl)
 // block size when no block size meets 2%.
 static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
 {
-    const long el = env_long("RADSORT_LAYOUT", 0);
-    const uint32_t want = pl->layout ? pl->layout : static_cast<uint32_t>(el);
-    if (want != RADSORT_LAYOUT_CHUNKS && n < (size_t(1) << 31)) {
+    if (pl->layout != RADSORT_LAYOUT_CHUNKS && n < (size_t(1) << 31)) {
         const uint32_t cands[] = {256, 512, 1024, 2048, 4096};
         size_t ws[5] = {};
         size_t least = 0;
@@ -209,9 +213,6 @@ static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
             pl->layout = RADSORT_LAYOUT_GRID;
             pl->block_size = best_b;
             pl->num_chunks = 1;
-            const long eb = env_long("RADSORT_B", 0);
-            if (eb > 0)
-                pl->block_size = static_cast<uint32_t>(eb);
             return;
         }
     }
@@ -222,10 +223,7 @@ static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
 static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl)
 {
     const size_t E = kb + vb;
-    double budget = 0.02 * double(n) * double(E);
-    const double floor_bytes = double(env_long("RADSORT_MIN_WS_MB", 0)) * (1 << 20);
-    if (budget < floor_bytes)
-        budget = floor_bytes;
+    const double budget = 0.02 * double(n) * double(E);
     uint32_t pcap = static_cast<uint32_t>(n / 65536);
     const uint32_t pmax = static_cast<uint32_t>(num_sms());
     if (pcap > pmax)
@@ -265,11 +263,6 @@ static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl)
     }
     pl->block_size = best_b;
     pl->num_chunks = best_p;
-    long eb = env_long("RADSORT_B", 0), ep = env_long("RADSORT_P", 0);
-    if (eb > 0)
-        pl->block_size = static_cast<uint32_t>(eb);
-    if (ep > 0)
-        pl->num_chunks = static_cast<uint32_t>(ep);
 }
 
 static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radsort_plan *plan,
@@ -457,9 +450,10 @@ static size_t workspace_of(size_t n, int kb, int vb, int db, const radsort_plan 
 }
 
 namespace {
-// autotuner cache: (ceil log2 n, key bytes, value bytes, digit bits) -> plan
+// autotuner cache: (device, ceil log2 n, key bytes, value bytes, digit bits)
+// -> plan (a plan's timing and chunk count depend on the device)
 struct TuneEntry {
-    int lg, kb, vb, db;
+    int dev, lg, kb, vb, db;
     radsort_plan plan;
 };
 constexpr int TUNE_CAP = 256;
@@ -716,12 +710,13 @@ radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t
     int lg = 0;
     while ((size_t(1) << lg) < n)
         ++lg;
+    const int dev = current_device();
     {
         // a cached plan is reused when it is valid for this n as well (the
         // limits of a layout can fall inside a size class)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         for (int i = 0; i < g_tune_n; ++i)
-            if (g_tune[i].lg == lg && g_tune[i].kb == key_bytes && g_tune[i].vb == vb &&
+            if (g_tune[i].dev == dev && g_tune[i].lg == lg && g_tune[i].kb == key_bytes && g_tune[i].vb == vb &&
                 g_tune[i].db == digit_bits && g_tune[i].plan.layout == base.layout &&
                 workspace_of(n, key_bytes, vb, digit_bits, g_tune[i].plan)) {
                 *plan = g_tune[i].plan;
@@ -797,13 +792,13 @@ radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t
         std::lock_guard<std::mutex> lk(g_tune_mu);
         int slot = -1;
         for (int i = 0; i < g_tune_n && slot < 0; ++i)
-            if (g_tune[i].lg == lg && g_tune[i].kb == key_bytes && g_tune[i].vb == vb &&
-                g_tune[i].db == digit_bits)
+            if (g_tune[i].dev == dev && g_tune[i].lg == lg && g_tune[i].kb == key_bytes &&
+                g_tune[i].vb == vb && g_tune[i].db == digit_bits)
                 slot = i; // replaces an entry that did not fit this n
         if (slot < 0 && g_tune_n < TUNE_CAP)
             slot = g_tune_n++;
         if (slot >= 0)
-            g_tune[slot] = TuneEntry{lg, key_bytes, vb, digit_bits, best};
+            g_tune[slot] = TuneEntry{dev, lg, key_bytes, vb, digit_bits, best};
     }
     *plan = best;
     return RADSORT_OK;
@@ -953,32 +948,22 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
 // Scratch of radsort_sort_noalloc: one array in this library's device image.
 // Every GPU that loads the library holds these bytes until the process
 // exits.  Host code must never pass the symbol itself to a kernel: on the
-// host it names a stand-in, not device memory.  The device address is taken
-// with cudaGetSymbolAddress once per device, below.
+// host it names a stand-in, not device memory.  Its device address is looked
+// up with cudaGetSymbolAddress on the current device at every call: the
+// lookup allocates nothing, and a context that was reset and created again
+// (cudaDeviceReset) may place the array elsewhere, so a cached address could
+// go stale.
 namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RADSORT_NOALLOC_SCRATCH_BYTES];
-std::mutex g_noalloc_mu;
-constexpr int NOALLOC_MAX_DEVICES = 64;
-void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
-// device address of the scratch on the current device (set up on first use)
+// device address of the scratch on the current device
 radsort_status noalloc_scratch(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
-        return RADSORT_EINVAL;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return e != cudaSuccess ? cuda_status(e) : RADSORT_ECUDA;
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return e != cudaSuccess ? cuda_status(e) : RADSORT_ECUDA;
+    *out = p;
     return RADSORT_OK;
 }
 

@@ -92,6 +92,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) accesses to the same bytes.  Every thread that
+// read or wrote a buffer with plain loads and stores executes it before the
+// barrier / mbarrier arrive that hands the buffer back to a bulk-copy issuer.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // 1-D bulk copy global -> shared through the TMA engine; completion is
 // signalled on `bar` as transaction bytes.  dst, src and bytes must be
 // multiples of 16.

@@ -797,6 +797,9 @@ __global__ void __launch_bounds__(FIN_T) k_fz_compact(FinArgs a, const uint4 *pl
                 }
             }
         }
+        // wk / wv were accessed with generic loads and stores; the next
+        // window may refill them with bulk copies (async proxy)
+        fence_proxy_async_smem();
         __syncthreads();
     }
 }
@@ -933,15 +936,19 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     const size_t msm = bbytes * L.K;
     const size_t kcap = L.W + 2 * (16 / g.kb) * (MAXSEG + 1), vcap = L.W + 8 * (MAXSEG + 1);
     const size_t csm = ((kcap * g.kb + 15) & ~size_t(15)) + (g.hasv ? vcap * 4 : 0);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fz_move<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
-        cudaFuncSetAttribute(k_fz_move_deferred<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             160 << 10);
-        cudaFuncSetAttribute(k_fz_compact<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             160 << 10);
-        attr = true;
-    }
+    static DeviceOnce attr;
+    const cudaError_t ea = attr.run([] {
+        cudaError_t e = cudaFuncSetAttribute(k_fz_move<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 << 10);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fz_move_deferred<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     160 << 10);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fz_compact<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     160 << 10);
+        return e;
+    });
+    if (ea != cudaSuccess)
+        return ea;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_move<KT>, FIN_T, msm);
     k_fz_move<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, msm, st>>>(a);

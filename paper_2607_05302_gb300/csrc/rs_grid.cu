@@ -216,17 +216,22 @@ __global__ void __launch_bounds__(1024) k_digit_hist_lanes(const KT *keys, uint3
 }
 
 // Launches the digit histograms for the key and digit widths.
-static void launch_digit_hist(const void *keys, uint32_t n, int kb, int db, uint32_t *hist, cudaStream_t st)
+static cudaError_t launch_digit_hist(const void *keys, uint32_t n, int kb, int db, uint32_t *hist,
+                                     cudaStream_t st)
 {
     using u64 = unsigned long long;
     if (db == 8) {
         constexpr int LSM = 4 * 256 * 32 * 4;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_digit_hist_lanes<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, LSM);
-            cudaFuncSetAttribute(k_digit_hist_lanes<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, LSM);
-            attr = true;
-        }
+        static DeviceOnce attr;
+        const cudaError_t ea = attr.run([] {
+            cudaError_t e = cudaFuncSetAttribute(k_digit_hist_lanes<uint32_t>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, LSM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_digit_hist_lanes<u64>, cudaFuncAttributeMaxDynamicSharedMemorySize, LSM);
+            return e;
+        });
+        if (ea != cudaSuccess)
+            return ea;
         const int grid = num_sms();
         if (kb == 4) {
             k_digit_hist_lanes<uint32_t><<<grid, 1024, LSM, st>>>(static_cast<const uint32_t *>(keys), n, 0, hist);
@@ -236,7 +241,7 @@ static void launch_digit_hist(const void *keys, uint32_t n, int kb, int db, uint
                 k_digit_hist_lanes<u64><<<grid, 1024, LSM, st>>>(static_cast<const u64 *>(keys), n, r0, hist);
             g_launches += 2;
         }
-        return;
+        return cudaGetLastError();
     }
     const int grid = num_sms() * 2;
     if (kb == 4)
@@ -244,6 +249,7 @@ static void launch_digit_hist(const void *keys, uint32_t n, int kb, int db, uint
     else
         k_digit_hist<u64, 11><<<grid, 512, 6 * 2048 * 4, st>>>(static_cast<const u64 *>(keys), n, hist);
     g_launches += 1;
+    return cudaGetLastError();
 }
 
 // Exclusive scan over an N-element array by a block of NT threads (each
@@ -1184,6 +1190,9 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 }
             }
         }
+        // the stage was read and rewritten with generic accesses; the
+        // producer refills it with bulk copies (async proxy)
+        fence_proxy_async_smem();
         bar();
         if (tid == 0)
             mbar_arrive(&empty[s]); // stage consumed: the producer may refill it
@@ -1195,13 +1204,12 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
 static int lb_ctas(size_t ntiles)
 {
     using C = LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_lb_round<KT, HASV, DB, TILE, NW, STAGES, OOP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM)) != cudaSuccess)
-            return -1;
-        attr = true;
-    }
+    static DeviceOnce attr; // per template instance
+    if (attr.run([] {
+            return cudaFuncSetAttribute(k_lb_round<KT, HASV, DB, TILE, NW, STAGES, OOP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+        }) != cudaSuccess)
+        return -1;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_round<KT, HASV, DB, TILE, NW, STAGES, OOP>,
                                                   C::THREADS, C::SMEM);
@@ -1281,7 +1289,9 @@ cudaError_t launch_grid_setup(const Geom &g, const Bufs &w, uint32_t *pi, cudaSt
         e = cudaMemsetAsync(w.status, 0, grid_ring_bytes(g), st);
     if (e != cudaSuccess)
         return e;
-    launch_digit_hist(w.Ak, static_cast<uint32_t>(g.n), g.kb, g.db, w.hist, st);
+    e = launch_digit_hist(w.Ak, static_cast<uint32_t>(g.n), g.kb, g.db, w.hist, st);
+    if (e != cudaSuccess)
+        return e;
     const uint32_t n = static_cast<uint32_t>(g.n);
     int blocks = static_cast<int>((g.npi + 255) / 256);
     if (blocks > 4096)
@@ -1393,16 +1403,18 @@ cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32
         e = cudaMemsetAsync(ctr, 0, 64 * 4, st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ringp, 0, ring_bytes(ntiles, sigma), st);
-    if (e != cudaSuccess)
-        return e;
     const uint32_t nn = static_cast<uint32_t>(n);
-    launch_digit_hist(keys, nn, kb, db, hist, st);
-    if (db == 8)
-        k_offsets<8><<<nt, 1024, 0, st>>>(hist, off, nn);
-    else
-        k_offsets<11><<<nt, 1024, 0, st>>>(hist, off, nn);
-    g_launches += 1;
-    e = lb_dispatch(kb, db, vals != nullptr, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int STAGES>() {
+    if (e == cudaSuccess)
+        e = launch_digit_hist(keys, nn, kb, db, hist, st);
+    if (e == cudaSuccess) {
+        if (db == 8)
+            k_offsets<8><<<nt, 1024, 0, st>>>(hist, off, nn);
+        else
+            k_offsets<11><<<nt, 1024, 0, st>>>(hist, off, nn);
+        g_launches += 1;
+    }
+    if (e == cudaSuccess)
+        e = lb_dispatch(kb, db, vals != nullptr, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int STAGES>() {
         using C = LbCfg<KT, HASV, DB, TILE, NW, STAGES, true>;
         const int grid = lb_ctas<KT, HASV, DB, TILE, NW, STAGES, true>(ntiles);
         if (grid < 0)
@@ -1429,12 +1441,13 @@ cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32
             std::swap(src, dst);
             std::swap(vs, vd);
         }
-        if (nt & 1) { // the result is in the alternate buffers: copy back
-            cudaMemcpyAsync(keys, src, n * sizeof(KT), cudaMemcpyDeviceToDevice, st);
-            if (HASV)
-                cudaMemcpyAsync(vals, vs, n * 4, cudaMemcpyDeviceToDevice, st);
+        cudaError_t ec = cudaGetLastError();
+        if (ec == cudaSuccess && (nt & 1)) { // the result is in the alternate buffers: copy back
+            ec = cudaMemcpyAsync(keys, src, n * sizeof(KT), cudaMemcpyDeviceToDevice, st);
+            if (ec == cudaSuccess && HASV)
+                ec = cudaMemcpyAsync(vals, vs, n * 4, cudaMemcpyDeviceToDevice, st);
         }
-        return cudaGetLastError();
+        return ec;
     });
     cudaError_t e2 = own ? cudaFreeAsync(scr, st) : cudaSuccess;
     return e != cudaSuccess ? e : e2;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 
 namespace rs {
 
@@ -107,7 +108,37 @@ cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long lon
                              size_t nseg, int kb, int db, void *scratch, cudaStream_t st);
 unsigned take_status_seg();
 
-int num_sms();
+// devices a process may use (per-device caches are sized for this many)
+constexpr int MAX_DEVICES = 64;
+int num_sms();     // SM count of the current device
+int current_device(); // current device ordinal, -1 on error
+
+// Runs a set-up step once per device (the device current at the call), for
+// example a cudaFuncSetAttribute opt-in: thread-safe, and repeated on a
+// device where it failed.  One object per call site (a function-local
+// static).
+class DeviceOnce {
+  public:
+    template <typename F> cudaError_t run(F &&f)
+    {
+        const int dev = current_device();
+        if (dev < 0 || dev >= MAX_DEVICES)
+            return cudaErrorInvalidDevice;
+        if (done_[dev].load(std::memory_order_acquire))
+            return cudaSuccess;
+        std::lock_guard<std::mutex> lk(mu_);
+        if (done_[dev].load(std::memory_order_relaxed))
+            return cudaSuccess;
+        const cudaError_t e = f();
+        if (e == cudaSuccess)
+            done_[dev].store(true, std::memory_order_release);
+        return e;
+    }
+
+  private:
+    std::mutex mu_;
+    std::atomic<bool> done_[MAX_DEVICES] = {};
+};
 // kernels launched by this library (host counter)
 extern std::atomic<unsigned long long> g_launches;
 // read and clear the device status words of each translation unit

@@ -613,6 +613,9 @@ __global__ void __launch_bounds__(RoundCfg<KT, HASV, DB, TILE, NW, STAGES>::THRE
                 }
             }
         }
+        // the stage was read and rewritten with generic accesses; the
+        // producer refills it with bulk copies (async proxy)
+        fence_proxy_async_smem();
         named_bar(1, NT);
         if (tid == 0)
             mbar_arrive(&empty[s]); // stage consumed: the producer may refill it
@@ -644,15 +647,14 @@ static cudaError_t round_impl(const Geom &g, const Bufs &w, const uint32_t *pi, 
                               uint32_t *UC, int round, cudaStream_t st)
 {
     using C = RoundCfg<KT, HASV, DB, TILE, NW, STAGES>;
-    static bool attr_set = false; // per template instance
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_round<KT, HASV, DB, TILE, NW, STAGES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(C::SMEM));
-        if (e != cudaSuccess)
-            return e;
-        attr_set = true;
-    }
+    static DeviceOnce attr; // per template instance
+    cudaError_t e0 = attr.run([] {
+        return cudaFuncSetAttribute(k_round<KT, HASV, DB, TILE, NW, STAGES>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(C::SMEM));
+    });
+    if (e0 != cudaSuccess)
+        return e0;
     RoundArgs<KT> a;
     a.Ak = static_cast<KT *>(w.Ak);
     a.Av = w.Av;

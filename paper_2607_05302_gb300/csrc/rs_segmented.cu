@@ -319,14 +319,17 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
     }
     static cudaError_t launch(const SegArgs &a, cudaStream_t st, int med_ctas)
     {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_seg_small<KT, HASV, DB, SMALL>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(small_smem()));
-            cudaFuncSetAttribute(k_seg_medium<KT, HASV, DB, TILE, SEG_MED>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(med_smem()));
-            attr = true;
-        }
+        static DeviceOnce attr;
+        const cudaError_t ea = attr.run([] {
+            cudaError_t e = cudaFuncSetAttribute(k_seg_small<KT, HASV, DB, SMALL>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(small_smem()));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_seg_medium<KT, HASV, DB, TILE, SEG_MED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(med_smem()));
+            return e;
+        });
+        if (ea != cudaSuccess)
+            return ea;
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_seg_small<KT, HASV, DB, SMALL>, SEG_T,
                                                       small_smem());
