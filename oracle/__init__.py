@@ -9,7 +9,8 @@ import this package; the CUDA library never does, and the two share no code.
 Every function is pinned in ``tests/test_oracle_pins.py`` to numpy's stable
 argsort, to brute-force stable sorting over exhaustive tiny inputs, and to the
 paper's data invariant (Sec. 2.2) and Lemmas 1-2; planted mistakes
-(``ORACLE_MUTANT``) show that the pins catch them.
+(``ORACLE_MUTANT``) show that the pins catch them, and state-only mistakes
+show that each invariant, Lemma and copy-bound check fires with its own code.
 """
 from __future__ import annotations
 
@@ -38,7 +39,11 @@ ERRORS = {
 
 
 class OracleError(RuntimeError):
-    pass
+    """A failed check of the oracle; ``code`` is the ORA_* error code."""
+
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 class Stats(ctypes.Structure):
@@ -98,7 +103,7 @@ def _ptr(a):
 
 def _check(rc: int):
     if rc != 0:
-        raise OracleError(ERRORS.get(rc, f"oracle error {rc}"))
+        raise OracleError(ERRORS.get(rc, f"oracle error {rc}"), rc)
 
 
 def _prep(keys, vals):

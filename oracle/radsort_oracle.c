@@ -54,6 +54,17 @@
 #ifndef ORACLE_MUTANT
 #define ORACLE_MUTANT 0 /* >0 plants a known mistake (used by the pin tests) */
 #endif
+/* Mutants 1-6 plant mistakes in the data path (caught by the output pins).
+ * Mutants 7-13 corrupt only the algorithm state, to show that each check of
+ * the data invariant (Sec. 2.2), of Lemmas 1-2 (Sec. 2.3) and of the copy
+ * bound (Sec. 3) fires on its own:
+ *   7  two P entries exchanged after fixupPhase   -> ORA_INV_PORDER
+ *   8  fill level f one past the last used block  -> ORA_INV_LASTPARTIAL
+ *   9  a block of pi' entered twice               -> ORA_INV_PERM
+ *   10 a head start of sigma-1 blocks per chunk   -> ORA_LEMMA1
+ *   11 one scratch block fewer (2H-1 blocks in T) -> ORA_LEMMA2
+ *   12 an open block's fill recorded one short    -> ORA_INV_COUNT
+ *   13 Finalize pulls through a bounce block      -> ORA_FIN_COPIES */
 
 /* error codes (negative) */
 #define ORA_OK 0
@@ -205,6 +216,7 @@ typedef struct {
     size_t n, b;
     uint64_t p;     /* chunks (Sec. 4.3); 1 = sequential algorithm */
     uint64_t H;     /* head start = sigma * p */
+    uint64_t tb;    /* scratch blocks in T: 2H */
     uint64_t n_pi;  /* floor(n/b) + 2H */
     elem_t *A;      /* input / output array */
     elem_t *T;      /* 2H scratch blocks */
@@ -221,14 +233,15 @@ typedef struct {
     uint32_t *U;    /* usage per free-list entry, U[q*U_stride + k] */
     uint64_t U_stride;
     uint64_t *iout; /* i_out per chunk */
+    elem_t *bounce; /* one block (mutant 13 only) */
     ora_stats *st;
 } rs_t;
 
 static elem_t *blockat(rs_t *s, uint64_t i)
 {
-    if (i < 2 * s->H)
+    if (i < s->tb)
         return &s->T[i * s->b];
-    return &s->A[(i - 2 * s->H) * s->b];
+    return &s->A[(i - s->tb) * s->b];
 }
 
 /* Alg. 3 with reading G1 */
@@ -285,10 +298,10 @@ static int setup(rs_t *s)
     for (uint64_t i = 0; i < H; i++) /* head start */
         s->pi[i] = i;
     for (uint64_t i = H; i + 1 < s->f; i++) /* contents of A */
-        s->pi[i] = 2 * H + (i - H);
+        s->pi[i] = s->tb + (i - H);
     for (uint64_t i = s->f - 1; i < s->n_pi; i++) /* remaining T blocks */
         s->pi[i] = H + (i - (s->f - 1));
-    memset(s->T, 0xA5, 2 * H * s->b * sizeof(elem_t)); /* reading G9 */
+    memset(s->T, 0xA5, s->tb * s->b * sizeof(elem_t)); /* reading G9 */
     memcpy(blockat(s, H), &s->A[nb * s->b], (s->n % s->b) * sizeof(elem_t)); /* tail */
     s->P[0].idx = s->f - 1;
     s->P[0].len = s->n % s->b;
@@ -351,6 +364,9 @@ static int sort_phase(rs_t *s, int t)
     uint64_t iP = 0;
     for (uint64_t q = 0; q < s->p; q++) {
         s->iout[q] = 0;
+#if ORACLE_MUTANT == 10
+        s->iout[q] = 1; /* planted state mistake: head start of sigma-1 blocks */
+#endif
         for (uint32_t c = 0; c < sigma; c++) { /* initial output blocks */
             int e = new_bucket_block(s, q, c, 0);
             if (e)
@@ -436,12 +452,27 @@ static int fixup_phase(rs_t *s)
             if (bk->end == blockat(s, phys) + s->b) { /* the open block? */
                 s->P[g].idx = s->S[g];
                 s->P[g].len = (uint64_t)(bk->next - blockat(s, phys));
+#if ORACLE_MUTANT == 12
+                if (s->P[g].len > 0) /* planted state mistake: fill one short */
+                    s->P[g].len--;
+#endif
             }
             s->S[g]++;
         }
     }
     s->nP = G;
     s->f = f_new;
+#if ORACLE_MUTANT == 7
+    if (G >= 2) { /* planted state mistake: two P entries exchanged */
+        partial_t x = s->P[0];
+        s->P[0] = s->P[G - 1];
+        s->P[G - 1] = x;
+    }
+#elif ORACLE_MUTANT == 8
+    s->f = f_new + 1; /* planted state mistake: f one past the last used block */
+#elif ORACLE_MUTANT == 9
+    s->pi2[0] = s->pi2[1]; /* planted state mistake: a block entered twice */
+#endif
     uint64_t *tmp = s->pi;
     s->pi = s->pi2;
     s->pi2 = tmp;
@@ -467,7 +498,7 @@ static int finalize(rs_t *s)
         pinv[s->pi[i]] = i;
     for (uint64_t i_in = H; i_in < H + nb; i_in++) {
         uint64_t j_in = s->pi[i_in];
-        uint64_t j_out = i_in + H; /* A block i_in - H (reading G2) */
+        uint64_t j_out = s->tb + (i_in - H); /* A block i_in - H (reading G2) */
         uint64_t i_out = pinv[j_out];
         if (i_in < i_out && i_out < s->f) { /* occupied by a block still needed */
 #if ORACLE_MUTANT != 4
@@ -479,7 +510,15 @@ static int finalize(rs_t *s)
             i_out = i_free; /* logical index now mapped to j_out (reading G3) */
         }
         uint64_t l = size_of_next_block(s, i_in, &iP);
+#if ORACLE_MUTANT == 13
+        /* planted mistake: the pull goes through a bounce block (the same
+         * data lands in A, at one more block copy each) */
+        memmove(s->bounce, blockat(s, j_in), l * sizeof(elem_t));
+        s->st->fin_copies_main++;
+        memmove(&s->A[k], s->bounce, l * sizeof(elem_t));
+#else
         memmove(&s->A[k], blockat(s, j_in), l * sizeof(elem_t)); /* pull (G6) */
+#endif
         s->st->fin_copies_main++;
         k += l;
         swap_blocks(s, pinv, i_out, j_out, i_in, j_in);
@@ -545,16 +584,21 @@ int ora_radsort(uint64_t *keys, uint32_t *vals, size_t n, int n_t, uint32_t sigm
     s.b = b;
     s.p = p;
     s.H = (uint64_t)sigma * p;
-    s.n_pi = n / b + 2 * s.H;
+    s.tb = 2 * s.H;
+#if ORACLE_MUTANT == 11
+    s.tb = 2 * s.H - 1; /* planted state mistake: one scratch block fewer */
+#endif
+    s.n_pi = n / b + s.tb;
     s.st = st;
     st->n_pi = s.n_pi;
     st->head = s.H;
-    st->t_blocks = 2 * s.H;
+    st->t_blocks = s.tb;
     st->min_unallocated = UINT64_MAX;
     uint64_t G = (uint64_t)sigma * p;
     s.U_stride = sigma + n / b + G + 2; /* >= sigma + longest chunk */
     s.A = malloc((n ? n : 1) * sizeof(elem_t));
-    s.T = malloc(2 * s.H * b * sizeof(elem_t));
+    s.T = malloc(s.tb * b * sizeof(elem_t));
+    s.bounce = malloc(b * sizeof(elem_t));
     s.pi = malloc(s.n_pi * sizeof(uint64_t));
     s.pi2 = malloc(s.n_pi * sizeof(uint64_t));
     s.P = malloc(G * sizeof(partial_t));
@@ -565,12 +609,13 @@ int ora_radsort(uint64_t *keys, uint32_t *vals, size_t n, int n_t, uint32_t sigm
     s.U = malloc(p * s.U_stride * sizeof(uint32_t));
     s.iout = malloc(p * sizeof(uint64_t));
     int err = ORA_OK;
-    if (!s.A || !s.T || !s.pi || !s.pi2 || !s.P || !s.lo || !s.C || !s.S || !s.B || !s.U || !s.iout) {
+    if (!s.A || !s.T || !s.pi || !s.pi2 || !s.P || !s.lo || !s.C || !s.S || !s.B || !s.U || !s.iout ||
+        !s.bounce) {
         err = ORA_ENOMEM;
         goto out;
     }
     /* Sec. 3/4 space: T, pi, pi' (reused as pi^-1), U, P, B, C, S */
-    st->extra_bytes = 2 * s.H * b * elem_bytes + s.n_pi * (4 + 4 + (sigma <= 256 ? 1 : 2)) +
+    st->extra_bytes = s.tb * b * elem_bytes + s.n_pi * (4 + 4 + (sigma <= 256 ? 1 : 2)) +
                       G * (8 /*P*/ + 16 /*B*/ + 4 /*C*/ + 4 /*S*/);
     for (size_t i = 0; i < n; i++) {
         s.A[i].key = keys[i];
@@ -598,7 +643,7 @@ int ora_radsort(uint64_t *keys, uint32_t *vals, size_t n, int n_t, uint32_t sigm
     }
 out:
     free(s.A), free(s.T), free(s.pi), free(s.pi2), free(s.P), free(s.lo);
-    free(s.C), free(s.S), free(s.B), free(s.U), free(s.iout);
+    free(s.C), free(s.S), free(s.B), free(s.U), free(s.iout), free(s.bounce);
     return err;
 }
 

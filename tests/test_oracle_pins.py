@@ -240,3 +240,55 @@ def test_planted_mistakes_are_caught(mutant):
     lib = oracle._lib(mutant)
     assert lib.ora_mutant_id() == mutant
     assert not _battery(mutant)
+
+
+# state-only mistakes: each corrupts the algorithm state in one place, and
+# the check written for that part of the state must fire with its own code
+# (data invariant of Sec. 2.2, Lemmas 1 and 2 of Sec. 2.3, copy bound of Sec. 3)
+STATE_MUTANTS = {
+    7: -13,   # two P entries exchanged -> invariant 2 (P ascending)
+    8: -14,   # f one past the last used block -> invariant 3 (block f-1 partial)
+    9: -12,   # a block entered twice in pi' -> invariant 1 (pi a permutation)
+    10: -10,  # head start of sigma-1 blocks -> Lemma 1
+    11: -11,  # one scratch block fewer -> Lemma 2
+    12: -15,  # an open block's fill one short -> invariant 5 (element count)
+    13: -17,  # Finalize pulls through a bounce block -> copy bound of Sec. 3
+}
+
+
+def _state_cases():
+    """Inputs on which the state mistakes meet their checks: random keys with
+    several block sizes and chunk counts, and one bucket that takes every
+    element (the tight case of Lemmas 1 and 2)."""
+    rng = np.random.default_rng(23)
+    out = []
+    for n, b, p in [(1000, 4, 1), (1000, 1, 1), (2000, 16, 3)]:
+        out.append((rng.integers(0, 2 ** 32, n, dtype=np.uint64), b, p))
+    out.append((np.full(1000, 0x12345678, np.uint64), 4, 1))
+    return out
+
+
+@pytest.mark.parametrize("mutant", sorted(STATE_MUTANTS))
+def test_state_mistakes_fire_their_own_check(mutant):
+    lib = oracle._lib(mutant)
+    assert lib.ora_mutant_id() == mutant
+    want = STATE_MUTANTS[mutant]
+    codes = set()
+    for keys, b, p in _state_cases():
+        vals = np.arange(keys.size, dtype=np.uint32)
+        try:
+            oracle.radsort(keys, vals, n_t=4, sigma=256, bits=8, b=b, p=p, mutant=mutant)
+            codes.add(0)
+        except oracle.OracleError as e:
+            codes.add(e.code)
+    # the intended check fires, and no other check claims the mistake
+    assert want in codes, (mutant, codes)
+    assert codes <= {0, want}, (mutant, codes)
+
+
+def test_clean_oracle_passes_the_state_cases():
+    for keys, b, p in _state_cases():
+        vals = np.arange(keys.size, dtype=np.uint32)
+        k, v = oracle.radsort(keys, vals, n_t=4, sigma=256, bits=8, b=b, p=p)
+        o = stable_ref(keys)
+        assert (v == o).all() and (k == keys[o]).all()
