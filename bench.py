@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Radsort benchmark on GB300.
 
-Default workload (N=1): n = 2^28 uint32 keys uniform over [0, 2^32) with a
-uint32 payload = original index, 8-bit digits (sigma = 256, n_t = 4 rounds).
+Default workload (N=1): n = 2^30 uint32 keys uniform over [0, 2^32) with a
+uint32 payload = original index, 8-bit digits (sigma = 256, n_t = 4 rounds),
+the size at which the round kernel's HBM roofline fraction is stated.
 One step = one full in-place Radsort: setup, 4 x (sortPhase, fixupPhase),
-Finalize.  Every timed step sorts its own fresh copy of the input (2 GiB,
-larger than L2), made before the timed region.
+Finalize.  Every timed step sorts its own fresh copy of the input (8 GiB,
+larger than L2), made before the timed region.  The other single-array
+workloads (2^28 uint32 keys; 2^30 uint64 keys with 8- and 11-bit digits) are
+timed after it with the comparator beside each, and reported under `extra`.
 
 Printed as one JSON line: device-resident throughput (value), end-to-end
 throughput through the public call with pinned host buffers, copies in and
@@ -44,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="radsort", choices=["radsort", "reference"])
-    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--log2n", type=int, default=30)
     ap.add_argument("--key-bytes", type=int, default=4, choices=[4, 8])
     ap.add_argument("--digit-bits", type=int, default=8, choices=[8, 11])
     ap.add_argument("--dist", default="uniform")
@@ -55,6 +58,8 @@ def parse():
     ap.add_argument("--no-oop", action="store_true", help="skip the out-of-place comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (2^28 u32, 2^30 u64 with 8- and 11-bit digits)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="radsort", choices=["radsort", "segmented", "serve"],
                     help="radsort: the headline line; segmented: 20,000 lognormal arrays in one "
@@ -208,11 +213,11 @@ def round_kernel_hash(files):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n, kb, db, lay):
+def profiled_traffic(n, kb, db, lay, bs):
     """DRAM bytes per round-kernel launch (dram__bytes_read.sum + write.sum)
     from the committed ncu summary of the layout's kernel, scaled from the
     captured size to n by the elements processed; None if the summary is
-    missing or older than the kernel."""
+    missing, older than the kernel, or taken at another block size."""
     name, files = ROUND_PROFILES["chunks" if lay == "chunks" else "grid"]
     try:
         txt = open(os.path.join(ROOT, "profiles", name)).read()
@@ -222,7 +227,10 @@ def profiled_traffic(n, kb, db, lay):
 
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(r"traffic_bytes_per_element:\s*([0-9.]+)", txt)
+    b = re.search(r"block_size:\s*([0-9]+)", txt)
     if not m or not t or m.group(1) != round_kernel_hash(files) or kb != 4 or db != 8:
+        return None
+    if not b or int(b.group(1)) != bs:
         return None
     return round(float(t.group(1)) * n)
 
@@ -398,6 +406,89 @@ def run_segmented(a):
     }), flush=True)
 
 
+def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream):
+    """One more single-array workload (uniform keys, index payload): Radsort
+    in the automatic plan and the out-of-place comparator on the same data,
+    each timed over `steps` fresh copies with CUDA events; the round kernel's
+    mean launch time from the library's trace gives its roofline fraction."""
+    import torch
+
+    n = 1 << log2n
+    E = kb + 4
+    r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=dev)
+    keys0 = ((r >> 32) & 0xFFFFFFFF).to(torch.int64).to(torch.int32) if kb == 4 else r
+    del r
+    vals0 = torch.arange(n, dtype=torch.int32, device=dev)
+    bs, pc, lay = R.radsort_plan_default(n, kb, 4, db)
+    wsb = R.radsort_workspace_size(n, kb, 4, db)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+    free_b = torch.cuda.mem_get_info(dev)[0]
+    nbuf = int(max(2, min(steps + warmup, (free_b * 0.4) // (n * E))))
+    kbufs = [torch.empty_like(keys0) for _ in range(nbuf)]
+    vbufs = [torch.empty_like(vals0) for _ in range(nbuf)]
+
+    def refill(i):
+        kbufs[i].copy_(keys0)
+        vbufs[i].copy_(vals0)
+
+    def run(fn):
+        for i in range(nbuf):
+            refill(i)
+        for i in range(warmup):
+            fn(i % nbuf)
+        for i in range(min(warmup, nbuf)):
+            refill(i)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(steps):
+            i = warmup + s
+            if i >= nbuf and s > 0:
+                refill(i % nbuf)
+            fn(i % nbuf)
+        e1.record(stream)
+        barrier()
+        R.radsort_device_status()
+        return e0.elapsed_time(e1) / steps
+
+    R.radsort_trace_read()
+    R.radsort_trace_enable(True)
+    ms = run(lambda i: R.sort_tensors(kbufs[i], vbufs[i], digit_bits=db, workspace=ws))
+    R.radsort_trace_enable(False)
+    recs = R.radsort_trace_read()
+    # the last step's result: sorted and a stable permutation of the input
+    last = (warmup + steps - 1) % nbuf
+    k = kbufs[last].to(torch.int64) & 0xFFFFFFFF if kb == 4 else kbufs[last] ^ (-(2 ** 63))
+    v = vbufs[last].to(torch.int64) & 0xFFFFFFFF
+    eq = kbufs[last][1:] == kbufs[last][:-1]
+    ok = bool((k[1:] >= k[:-1]).all()) and bool(torch.equal(keys0[v], kbufs[last])) and bool(
+        (v[1:][eq] > v[:-1][eq]).all())
+    del k, v, eq
+    rounds = [t for ph, rd, t in recs if ph == "sortPhase"]
+    fin = [t for ph, rd, t in recs if ph == "Finalize"]
+    avg_round = statistics.mean(rounds) if rounds else float("nan")
+    hbm, src = peaks()
+    ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
+    oms = run(lambda i: R.lsd_oop_tensors(kbufs[i], vbufs[i], ka, va, digit_bits=db))
+    val = n / (ms / 1e3) / 1e9
+    oval = n / (oms / 1e3) / 1e9
+    out = {
+        "workload": f"radsort_{'u32' if kb == 4 else 'u64'}_keys_u32_index_2^{log2n}_uniform_d{db}",
+        "n": n, "value": round(val, 3), "unit": "Gkeys/s", "ms_per_step": round(ms, 3), "steps": steps,
+        "block_size": bs, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
+        "round_ms": round(avg_round, 4),
+        "round_frac": round((n * 2 * E) / (avg_round / 1e3) / 1e9 / hbm, 4),
+        "finalize_ms": round(statistics.mean(fin), 4) if fin else None,
+        "result_checked": ok,
+        "oop": {"value": round(oval, 3), "ms_per_step": round(oms, 3),
+                "extra_bytes": n * E + R.radsort_lsd_oop_scratch_size(n, kb, 4, db)},
+        "radsort_over_oop": round(val / oval, 4),
+    }
+    del kbufs, vbufs, ws, ka, va, keys0, vals0
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     a = parse()
@@ -528,7 +619,7 @@ def main():
     avg_round = statistics.mean(round_ms) if round_ms else float("nan")
     hbm, src = peaks()
     achieved = (n * 2 * E) / (avg_round / 1e3) / 1e9
-    traffic = profiled_traffic(n, kb, db, lay)
+    traffic = profiled_traffic(n, kb, db, lay, bs)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "kernel": ("k_round (sortPhase, Alg. 5, chunk layout)" if lay == "chunks"
@@ -603,6 +694,21 @@ def main():
                "radsort_over_oop": round(value / oval, 4)}
         del ka, va
 
+    # ---- the other single-array workloads, each with its comparator
+    extra = None
+    if not a.no_extra and world == 1:
+        kbufs.clear()
+        vbufs.clear()
+        del ws
+        torch.cuda.empty_cache()
+        extra = {}
+        for lg, kb2, db2 in ((28, 4, 8), (30, 8, 8), (30, 8, 11)):
+            if (lg, kb2, db2) == (a.log2n, kb, db):
+                continue
+            key = f"{'u32' if kb2 == 4 else 'u64'}_2^{lg}_d{db2}"
+            extra[key] = time_workload(R, W, dev, lg, kb2, db2, min(a.steps, 6), max(3, min(a.warmup, 3)),
+                                       barrier, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         rate, sample, el = oracle_sample_rate(a, a.cpu_seconds)
@@ -619,10 +725,11 @@ def main():
                        "digit_bits": db, "layout": "chunks" if lay == "chunks" else "grid",
                        "block_size": bs, "num_chunks": pc,
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2: each timed step sorts its own fresh 2^%d-element copy" % a.log2n},
+                       "l2": "inputs larger than L2: each timed step sorts its own fresh 2^%d-element copy" % a.log2n,
+                       "extra": "uniform keys, automatic plan, comparator beside each; fresh copies per step"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
-            "oop": oop, "chunk_layout": plan2,
+            "oop": oop, "chunk_layout": plan2, "extra": extra,
             "phases_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
             "algorithmic_bytes_per_step": step_bytes,
         }

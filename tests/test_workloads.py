@@ -67,3 +67,28 @@ def test_serving_footprints():
         elif req.n >= 1 << 22:
             assert r <= 1.12 * req.n * E
     assert big > 100
+
+
+def test_oracle_jobs_match_a_stable_argsort(tmp_path):
+    """The worker that computes the full-size parity expectations, run on
+    small sizes: its files hold the stable sort of the seeded inputs."""
+    import sys
+    import os
+
+    sys.path.insert(0, os.path.dirname(__file__))
+    import oracle_jobs
+
+    n = 1 << 14
+    for job in [("u32", d, 14) for d in W.DISTRIBUTIONS] + [("u64", 8, 14), ("u64", 11, 14)]:
+        pk, pv = oracle_jobs.run(job, str(tmp_path))
+        k, v = np.load(pk), np.load(pv)
+        if job[0] == "u32":
+            host = W.make_keys(job[1], n)
+            order_keys = host
+            if job[1] == "float":  # IEEE total order via the sign-flip transform
+                order_keys = np.where(host >> np.uint32(31), ~host, host | np.uint32(1 << 31))
+        else:
+            host = order_keys = W.make_keys("uniform", n, 64)
+        o = np.argsort(order_keys, kind="stable")
+        assert np.array_equal(v, o.astype(np.uint32)), job
+        assert np.array_equal(k, host[o]), job
