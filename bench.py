@@ -213,16 +213,18 @@ def round_kernel_hash(files):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n, kb, db, lay, bs):
+def profiled_traffic(n, kb, db, lay, bs, text=None):
     """DRAM bytes per round-kernel launch (dram__bytes_read.sum + write.sum)
     from the committed ncu summary of the layout's kernel, scaled from the
     captured size to n by the elements processed; None if the summary is
     missing, older than the kernel, or taken at another block size."""
     name, files = ROUND_PROFILES["chunks" if lay == "chunks" else "grid"]
-    try:
-        txt = open(os.path.join(ROOT, "profiles", name)).read()
-    except OSError:
-        return None
+    txt = text
+    if txt is None:
+        try:
+            txt = open(os.path.join(ROOT, "profiles", name)).read()
+        except OSError:
+            return None
     import re
 
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)

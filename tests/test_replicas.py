@@ -56,22 +56,20 @@ def test_one_process_needs_no_collective():
 
 def test_profiled_traffic_follows_the_kernel_sources(monkeypatch):
     """The roofline's traffic comes from the committed ncu summary only while
-    its source hash matches the round kernel's sources: scaled by elements
-    (bytes per element x n) when it does, None after any change to them, and
-    None for configurations the summary does not cover."""
-    import re
-
+    its source hash matches the round kernel's sources and its block size is
+    the bench's: scaled by elements (bytes per element x n) when they do, None
+    after any change to the sources, at another block size, and for
+    configurations the summary does not cover."""
     import bench
 
-    name, _ = bench.ROUND_PROFILES["grid"]
-    txt = open(os.path.join(bench.ROOT, "profiles", name)).read()
-    recorded = re.search(r"source_hash:\s*([0-9a-f]+)", txt).group(1)
+    txt = "source_hash: 0123456789abcdef\ntraffic_bytes_per_element: 15.5\nblock_size: 2048\n"
     n = 1 << 28
-    monkeypatch.setattr(bench, "round_kernel_hash", lambda files: recorded)
-    t = bench.profiled_traffic(n, 4, 8, "grid")
-    assert t is not None and 15.0 * n <= t <= 16.5 * n  # no re-reads beyond 16 B/element
-    assert bench.profiled_traffic(n // 2, 4, 8, "grid") == pytest.approx(t / 2, rel=1e-6)
-    assert bench.profiled_traffic(n, 8, 8, "grid") is None
-    assert bench.profiled_traffic(n, 4, 11, "grid") is None
+    monkeypatch.setattr(bench, "round_kernel_hash", lambda files: "0123456789abcdef")
+    t = bench.profiled_traffic(n, 4, 8, "grid", 2048, text=txt)
+    assert t == round(15.5 * n)
+    assert bench.profiled_traffic(n // 2, 4, 8, "grid", 2048, text=txt) == pytest.approx(t / 2, rel=1e-6)
+    assert bench.profiled_traffic(n, 4, 8, "grid", 1024, text=txt) is None
+    assert bench.profiled_traffic(n, 8, 8, "grid", 2048, text=txt) is None
+    assert bench.profiled_traffic(n, 4, 11, "grid", 2048, text=txt) is None
     monkeypatch.setattr(bench, "round_kernel_hash", lambda files: "0" * 16)
-    assert bench.profiled_traffic(n, 4, 8, "grid") is None
+    assert bench.profiled_traffic(n, 4, 8, "grid", 2048, text=txt) is None
