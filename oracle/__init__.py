@@ -57,6 +57,7 @@ class Stats(ctypes.Structure):
         ("fin_copies_rest", ctypes.c_uint64),
         ("fin_pushes", ctypes.c_uint64),
         ("extra_bytes", ctypes.c_uint64),
+        ("fin_copies_trunc", ctypes.c_uint64),
     ]
 
     def as_dict(self):
@@ -93,6 +94,21 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
         lib.ora_f32_to_ordered.argtypes = [P, ctypes.c_size_t]
         lib.ora_ordered_to_f32.argtypes = [P, ctypes.c_size_t]
         lib.ora_mutant_id.restype = ctypes.c_int
+        lib.ora_perm_new.argtypes = [P, P, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                                     ctypes.c_size_t, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_int)]
+        lib.ora_perm_new.restype = ctypes.c_void_p
+        lib.ora_perm_free.argtypes = [P]
+        lib.ora_perm_rounds.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        lib.ora_perm_rounds.restype = ctypes.c_int
+        lib.ora_perm_count.argtypes = [P]
+        lib.ora_perm_count.restype = ctypes.c_uint64
+        lib.ora_perm_gather.argtypes = [P, P, P]
+        lib.ora_perm_truncate.argtypes = [P, ctypes.c_uint64]
+        lib.ora_perm_truncate.restype = ctypes.c_int
+        lib.ora_perm_finalize.argtypes = [P, P, P]
+        lib.ora_perm_finalize.restype = ctypes.c_int
+        lib.ora_perm_stats.argtypes = [P, ctypes.POINTER(Stats)]
         _libs[mutant] = lib
     return _libs[mutant]
 
@@ -157,3 +173,57 @@ def ordered_to_f32(u32):
     a = np.ascontiguousarray(u32).astype(np.uint32, copy=True)
     _lib().ora_ordered_to_f32(_ptr(a), a.size)
     return a
+
+
+class Perm:
+    """The permuted representation kept between calls (Sec. 4.1): setup
+    (Alg. 4) on construction, then rounds (Alg. 5-6), truncate (Alg. 8), the
+    logical sequence (Alg. 3 walk) and Finalize (Alg. 7)."""
+
+    def __init__(self, keys, vals=None, *, n_t, sigma, bits, b, p=1, elem_bytes=8, mutant=0):
+        k, v = _prep(keys, vals)
+        self._lib = _lib(mutant)
+        self.has_vals = v is not None
+        err = ctypes.c_int(0)
+        self._h = self._lib.ora_perm_new(_ptr(k), _ptr(v), k.size, n_t, sigma, bits, b, p, elem_bytes,
+                                         ctypes.byref(err))
+        if not self._h:
+            _check(err.value or -2)
+
+    def close(self):
+        if self._h:
+            self._lib.ora_perm_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __len__(self):
+        return int(self._lib.ora_perm_count(self._h))
+
+    def rounds(self, first, count):
+        """Rounds first .. first+count-1 (round r sorts by digit n_t-1-r)."""
+        _check(self._lib.ora_perm_rounds(self._h, first, count))
+
+    def truncate(self, m):
+        """Keeps the first m elements of the logical sequence (Alg. 8)."""
+        _check(self._lib.ora_perm_truncate(self._h, m))
+
+    def sequence(self):
+        n = len(self)
+        sk = np.zeros(n, np.uint64)
+        sv = np.zeros(n, np.uint32) if self.has_vals else None
+        self._lib.ora_perm_gather(self._h, _ptr(sk), _ptr(sv))
+        return sk, sv
+
+    def finalize(self):
+        n = len(self)
+        k = np.zeros(max(n, 1), np.uint64)
+        v = np.zeros(max(n, 1), np.uint32)
+        _check(self._lib.ora_perm_finalize(self._h, _ptr(k), _ptr(v)))
+        return k[:n], (v[:n] if self.has_vals else None)
+
+    def stats(self):
+        st = Stats()
+        self._lib.ora_perm_stats(self._h, ctypes.byref(st))
+        return st.as_dict()

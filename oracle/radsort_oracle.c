@@ -42,6 +42,15 @@
  *      fails by one at block ends, e.g. b = 1).
  *   G9 T and unallocated blocks are poisoned (0xA5 bytes) so that a read of
  *      unallocated data shows up in the output.
+ *   G15 Alg. 8 (truncate) drops the P entries after the one it rewrites, and
+ *      a cut at a block's last element makes the next logical block the
+ *      final, empty partial block (see truncate_at).
+ *   G16 Finalize after a truncation pushes a remaining block out of A block
+ *      floor(n/b) before the gap-closing copies (see finalize).
+ *
+ *   ora_perm_*    -- the permuted representation kept between calls
+ *                    (Sec. 4.1): rounds on it, truncate (Alg. 8), the
+ *                    logical sequence, and a later Finalize.
  *
  * Function pins (tests/test_oracle_pins.py): every function here is pinned
  * to numpy's stable argsort, to brute-force stable sorting of exhaustive
@@ -64,7 +73,10 @@
  *   10 a head start of sigma-1 blocks per chunk   -> ORA_LEMMA1
  *   11 one scratch block fewer (2H-1 blocks in T) -> ORA_LEMMA2
  *   12 an open block's fill recorded one short    -> ORA_INV_COUNT
- *   13 Finalize pulls through a bounce block      -> ORA_FIN_COPIES */
+ *   13 Finalize pulls through a bounce block      -> ORA_FIN_COPIES
+ * Mutants 14-15 concern truncation (Alg. 8) and Finalize after it:
+ *   14 truncate keeps a P entry past the new end  -> ORA_INV_PORDER
+ *   15 Finalize without the push of reading G16   -> wrong output */
 
 /* error codes (negative) */
 #define ORA_OK 0
@@ -94,6 +106,7 @@ typedef struct {
     uint64_t fin_copies_rest; /* block copies in Finalize's second loop */
     uint64_t fin_pushes;
     uint64_t extra_bytes;   /* T + bookkeeping, Sec. 3 "Space" / Sec. 4 */
+    uint64_t fin_copies_trunc; /* Finalize's push out of A block floor(n/b) (reading G16) */
 } ora_stats;
 
 /* ---- key positions (Sec. 1; reading G8) -------------------------------- */
@@ -527,7 +540,30 @@ static int finalize(rs_t *s)
             j_free = j_in;
         }
     }
-    for (uint64_t i_in = H + nb; i_in < s->f; i_in++) { /* remaining blocks, all in T */
+    /* reading G16: after a truncation (Alg. 8) physical A blocks nb .. hold
+     * no data of the sequence's prefix, and a remaining block may sit in A
+     * block nb, which the copies below overwrite (the untruncated sequence
+     * has no A block nb).  Such a block is first pushed, as Alg. 7 pushes
+     * occupants, to an unallocated block outside A[0 .. (nb+1)b). */
+    uint64_t j_cut = s->tb + nb;
+#if ORACLE_MUTANT == 15
+    j_cut = s->n_pi; /* planted mistake: reading G16 left out */
+#endif
+    if (j_cut < s->n_pi && pinv[j_cut] >= H + nb && pinv[j_cut] < s->f) {
+        uint64_t i_cut = pinv[j_cut], i_to = s->n_pi;
+        for (uint64_t i = 0; i < s->n_pi && i_to == s->n_pi; i++)
+            if ((i < H || i >= s->f) && (s->pi[i] < s->tb || s->pi[i] > j_cut))
+                i_to = i;
+        if (i_to == s->n_pi)
+            return ORA_FIN_COUNT;
+        uint64_t j_to = s->pi[i_to];
+        memcpy(blockat(s, j_to), blockat(s, j_cut), b * sizeof(elem_t));
+        s->st->fin_pushes++;
+        s->st->fin_copies_trunc++;
+        swap_blocks(s, pinv, i_cut, j_cut, i_to, j_to);
+    }
+    /* remaining blocks: in T, or (after a truncation) in A blocks past nb */
+    for (uint64_t i_in = H + nb; i_in < s->f; i_in++) {
         uint64_t j_in = s->pi[i_in];
         uint64_t l = size_of_next_block(s, i_in, &iP);
         memmove(&s->A[k], blockat(s, j_in), l * sizeof(elem_t));
@@ -558,6 +594,79 @@ static void gather_sequence(rs_t *s, uint64_t *seq_keys, uint32_t *seq_vals)
     }
 }
 
+/* allocation of the state and setup (Alg. 4) on a copy of keys/vals */
+static int rs_open(rs_t *s, ora_stats *st, const uint64_t *keys, const uint32_t *vals, size_t n,
+                   int n_t, uint32_t sigma, int bits, size_t b, uint64_t p, uint64_t elem_bytes)
+{
+    keyspec ks = {n_t, sigma, bits};
+    memset(st, 0, sizeof(*st));
+    memset(s, 0, sizeof(*s));
+    if (check_spec(&ks) != ORA_OK || b < 1 || p < 1)
+        return ORA_EARG;
+    s->ks = ks;
+    s->n = n;
+    s->b = b;
+    s->p = p;
+    s->H = (uint64_t)sigma * p;
+    s->tb = 2 * s->H;
+#if ORACLE_MUTANT == 11
+    s->tb = 2 * s->H - 1; /* planted state mistake: one scratch block fewer */
+#endif
+    s->n_pi = n / b + s->tb;
+    s->st = st;
+    st->n_pi = s->n_pi;
+    st->head = s->H;
+    st->t_blocks = s->tb;
+    st->min_unallocated = UINT64_MAX;
+    uint64_t G = (uint64_t)sigma * p;
+    s->U_stride = sigma + n / b + G + 2; /* >= sigma + longest chunk */
+    s->A = malloc((n ? n : 1) * sizeof(elem_t));
+    s->T = malloc(s->tb * b * sizeof(elem_t));
+    s->bounce = malloc(b * sizeof(elem_t));
+    s->pi = malloc(s->n_pi * sizeof(uint64_t));
+    s->pi2 = malloc(s->n_pi * sizeof(uint64_t));
+    s->P = malloc(G * sizeof(partial_t));
+    s->lo = malloc((p + 1) * sizeof(uint64_t));
+    s->C = malloc(G * sizeof(uint64_t));
+    s->S = malloc(G * sizeof(uint64_t));
+    s->B = malloc(G * sizeof(bucket_t));
+    s->U = malloc(p * s->U_stride * sizeof(uint32_t));
+    s->iout = malloc(p * sizeof(uint64_t));
+    if (!s->A || !s->T || !s->pi || !s->pi2 || !s->P || !s->lo || !s->C || !s->S || !s->B ||
+        !s->U || !s->iout || !s->bounce)
+        return ORA_ENOMEM;
+    /* Sec. 3/4 space: T, pi, pi' (reused as pi^-1), U, P, B, C, S */
+    st->extra_bytes = s->tb * b * elem_bytes + s->n_pi * (4 + 4 + (sigma <= 256 ? 1 : 2)) +
+                      G * (8 /*P*/ + 16 /*B*/ + 4 /*C*/ + 4 /*S*/);
+    for (size_t i = 0; i < n; i++) {
+        s->A[i].key = keys[i];
+        s->A[i].val = vals ? vals[i] : 0;
+    }
+    return setup(s);
+}
+
+static void rs_close(rs_t *s)
+{
+    free(s->A), free(s->T), free(s->pi), free(s->pi2), free(s->P), free(s->lo);
+    free(s->C), free(s->S), free(s->B), free(s->U), free(s->iout), free(s->bounce);
+    memset(s, 0, sizeof(*s));
+}
+
+/* rounds first .. first+count-1 of Alg. 2's loop: sortPhase (Alg. 5) on
+ * digit t = n_t-1-r, then fixupPhase (Alg. 6) */
+static int run_rounds(rs_t *s, int first, int count)
+{
+    if (first < 0 || count < 0 || first + count > s->ks.n_t)
+        return ORA_EARG;
+    int err = ORA_OK;
+    for (int r = first; r < first + count && !err; r++) {
+        err = sort_phase(s, s->ks.n_t - 1 - r);
+        if (!err)
+            err = fixup_phase(s);
+    }
+    return err;
+}
+
 /*
  * Alg. 2 (radSort).  Runs setup and `rounds` rounds (t = n_t-1 downwards).
  * finalize != 0: Finalize, result in keys/vals (needs rounds == n_t for a
@@ -570,81 +679,160 @@ int ora_radsort(uint64_t *keys, uint32_t *vals, size_t n, int n_t, uint32_t sigm
                 size_t b, uint64_t p, int rounds, int do_finalize, uint64_t *seq_keys,
                 uint32_t *seq_vals, uint64_t elem_bytes, ora_stats *st)
 {
-    keyspec ks = {n_t, sigma, bits};
     ora_stats dummy;
     if (!st)
         st = &dummy;
-    memset(st, 0, sizeof(*st));
-    if (check_spec(&ks) != ORA_OK || b < 1 || p < 1 || rounds < 0 || rounds > n_t)
+    if (rounds < 0 || rounds > n_t) {
+        memset(st, 0, sizeof(*st));
         return ORA_EARG;
+    }
     rs_t s;
-    memset(&s, 0, sizeof(s));
-    s.ks = ks;
-    s.n = n;
-    s.b = b;
-    s.p = p;
-    s.H = (uint64_t)sigma * p;
-    s.tb = 2 * s.H;
-#if ORACLE_MUTANT == 11
-    s.tb = 2 * s.H - 1; /* planted state mistake: one scratch block fewer */
-#endif
-    s.n_pi = n / b + s.tb;
-    s.st = st;
-    st->n_pi = s.n_pi;
-    st->head = s.H;
-    st->t_blocks = s.tb;
-    st->min_unallocated = UINT64_MAX;
-    uint64_t G = (uint64_t)sigma * p;
-    s.U_stride = sigma + n / b + G + 2; /* >= sigma + longest chunk */
-    s.A = malloc((n ? n : 1) * sizeof(elem_t));
-    s.T = malloc(s.tb * b * sizeof(elem_t));
-    s.bounce = malloc(b * sizeof(elem_t));
-    s.pi = malloc(s.n_pi * sizeof(uint64_t));
-    s.pi2 = malloc(s.n_pi * sizeof(uint64_t));
-    s.P = malloc(G * sizeof(partial_t));
-    s.lo = malloc((p + 1) * sizeof(uint64_t));
-    s.C = malloc(G * sizeof(uint64_t));
-    s.S = malloc(G * sizeof(uint64_t));
-    s.B = malloc(G * sizeof(bucket_t));
-    s.U = malloc(p * s.U_stride * sizeof(uint32_t));
-    s.iout = malloc(p * sizeof(uint64_t));
-    int err = ORA_OK;
-    if (!s.A || !s.T || !s.pi || !s.pi2 || !s.P || !s.lo || !s.C || !s.S || !s.B || !s.U || !s.iout ||
-        !s.bounce) {
-        err = ORA_ENOMEM;
-        goto out;
+    int err = rs_open(&s, st, keys, vals, n, n_t, sigma, bits, b, p, elem_bytes);
+    if (!err)
+        err = run_rounds(&s, 0, rounds);
+    if (!err) {
+        if (do_finalize) {
+            err = finalize(&s);
+            for (size_t i = 0; !err && i < n; i++) {
+                keys[i] = s.A[i].key;
+                if (vals)
+                    vals[i] = s.A[i].val;
+            }
+        } else {
+            gather_sequence(&s, seq_keys, seq_vals);
+        }
     }
-    /* Sec. 3/4 space: T, pi, pi' (reused as pi^-1), U, P, B, C, S */
-    st->extra_bytes = s.tb * b * elem_bytes + s.n_pi * (4 + 4 + (sigma <= 256 ? 1 : 2)) +
-                      G * (8 /*P*/ + 16 /*B*/ + 4 /*C*/ + 4 /*S*/);
-    for (size_t i = 0; i < n; i++) {
-        s.A[i].key = keys[i];
-        s.A[i].val = vals ? vals[i] : 0;
-    }
-    err = setup(&s);
-    for (int r = 0; r < rounds && !err; r++) {
-        err = sort_phase(&s, n_t - 1 - r);
-        if (!err)
-            err = fixup_phase(&s);
+    rs_close(&s);
+    return err;
+}
+
+/* ======================================================================
+ * The permuted representation kept between calls (Sec. 4.1): rounds on it,
+ * truncation (Alg. 8), reading it in logical order, and a later Finalize.
+ * ====================================================================== */
+typedef struct {
+    rs_t s;
+    ora_stats st;
+} perm_t;
+
+/* setup (Alg. 4) on a copy of keys/vals; NULL on a bad argument or no memory */
+void *ora_perm_new(const uint64_t *keys, const uint32_t *vals, size_t n, int n_t, uint32_t sigma,
+                   int bits, size_t b, uint64_t p, uint64_t elem_bytes, int *err)
+{
+    perm_t *h = malloc(sizeof(perm_t));
+    int e = h ? rs_open(&h->s, &h->st, keys, vals, n, n_t, sigma, bits, b, p, elem_bytes) : ORA_ENOMEM;
+    if (e && h) {
+        rs_close(&h->s);
+        free(h);
+        h = NULL;
     }
     if (err)
-        goto out;
-    if (do_finalize) {
-        err = finalize(&s);
-        if (err)
-            goto out;
-        for (size_t i = 0; i < n; i++) {
-            keys[i] = s.A[i].key;
-            if (vals)
-                vals[i] = s.A[i].val;
-        }
-    } else {
-        gather_sequence(&s, seq_keys, seq_vals);
+        *err = e;
+    return h;
+}
+
+void ora_perm_free(void *hp)
+{
+    perm_t *h = hp;
+    if (h) {
+        rs_close(&h->s);
+        free(h);
     }
-out:
-    free(s.A), free(s.T), free(s.pi), free(s.pi2), free(s.P), free(s.lo);
-    free(s.C), free(s.S), free(s.B), free(s.U), free(s.iout), free(s.bounce);
+}
+
+int ora_perm_rounds(void *hp, int first, int count)
+{
+    perm_t *h = hp;
+    return run_rounds(&h->s, first, count);
+}
+
+uint64_t ora_perm_count(void *hp)
+{
+    return ((perm_t *)hp)->s.n;
+}
+
+/* the logical sequence, n entries (Alg. 3 walk) */
+void ora_perm_gather(void *hp, uint64_t *seq_keys, uint32_t *seq_vals)
+{
+    gather_sequence(&((perm_t *)hp)->s, seq_keys, seq_vals);
+}
+
+/*
+ * Alg. 8: truncate the dataset so that logical block i, element j is the
+ * final datum.  f becomes i+1 and the first partial block at or after i
+ * becomes (i, j+1).  Readings:
+ *   G15 the P entries after that one describe blocks past the new end and
+ *       are dropped (nP = its index + 1); a cut at a block's last element
+ *       (j+1 = b) leaves block i full, so logical block i+1 becomes the final
+ *       block, partial with length 0 (clause 3 of the invariant, Sec. 2.2,
+ *       wants block f-1 partial); the element count n is the count up to the
+ *       cut.
+ * ora_perm_truncate(h, m) keeps the first m <= n elements: (i, j) is the
+ * position of element m-1 in the walk of Alg. 3; m = 0 leaves one empty
+ * partial block at logical index H.
+ */
+static int truncate_at(rs_t *s, uint64_t i, uint64_t j, uint64_t m)
+{
+    s->f = i + 1; /* mark logical block i as the final block */
+    for (uint64_t iP = 0; iP < s->nP; iP++) { /* skip partial blocks before i */
+        if (i <= s->P[iP].idx) {
+            s->P[iP].idx = i; /* logical block i ends at element j */
+            s->P[iP].len = j + 1;
+            s->nP = iP + 1;
+#if ORACLE_MUTANT == 14
+            s->nP = iP + 2 <= s->ks.sigma * s->p ? iP + 2 : iP + 1; /* planted: a stale entry kept */
+#endif
+            if (j + 1 == s->b) { /* reading G15: block i is full */
+                s->P[iP].idx = i + 1;
+                s->P[iP].len = 0;
+                s->f = i + 2;
+            }
+            s->n = m;
+            return check_invariant(s);
+        }
+    }
+    return ORA_INV_PORDER; /* no partial block at or after i: not a valid state */
+}
+
+int ora_perm_truncate(void *hp, uint64_t m)
+{
+    rs_t *s = &((perm_t *)hp)->s;
+    if (m > s->n)
+        return ORA_EARG;
+    if (m == 0) {
+        s->f = s->H + 1;
+        s->P[0].idx = s->H;
+        s->P[0].len = 0;
+        s->nP = 1;
+        s->n = 0;
+        return check_invariant(s);
+    }
+    uint64_t iP = 0, pos = 0;
+    for (uint64_t i = s->H; i < s->f; i++) {
+        uint64_t l = size_of_next_block(s, i, &iP);
+        if (m - 1 < pos + l)
+            return truncate_at(s, i, m - 1 - pos, m);
+        pos += l;
+    }
+    return ORA_INV_COUNT;
+}
+
+/* Alg. 7 on the current state; keys/vals receive A[0..n) */
+int ora_perm_finalize(void *hp, uint64_t *keys, uint32_t *vals)
+{
+    rs_t *s = &((perm_t *)hp)->s;
+    int err = finalize(s);
+    for (size_t i = 0; !err && i < s->n; i++) {
+        keys[i] = s->A[i].key;
+        if (vals)
+            vals[i] = s->A[i].val;
+    }
     return err;
+}
+
+void ora_perm_stats(void *hp, ora_stats *out)
+{
+    *out = ((perm_t *)hp)->st;
 }
 
 /* order-preserving bit transform of float32 keys (not in the paper): the

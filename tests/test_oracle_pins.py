@@ -292,3 +292,89 @@ def test_clean_oracle_passes_the_state_cases():
         k, v = oracle.radsort(keys, vals, n_t=4, sigma=256, bits=8, b=b, p=p)
         o = stable_ref(keys)
         assert (v == o).all() and (k == keys[o]).all()
+
+
+# ---------------------------------------------------------------- truncate (Alg. 8)
+def _perm(keys, vals, b, p, mutant=0):
+    return oracle.Perm(keys, vals, n_t=4, sigma=256, bits=8, b=b, p=p, mutant=mutant)
+
+
+@pytest.mark.parametrize("b,p", [(1, 1), (4, 1), (16, 1), (64, 3), (8, 5)])
+def test_truncate_keeps_the_prefix(b, p):
+    """After r rounds the logical sequence is r rounds of Alg. 1; truncating
+    it to m elements (Alg. 8) leaves exactly its first m elements, and the
+    state still satisfies the data invariant (checked inside the oracle)."""
+    rng = np.random.default_rng(100 + b + p)
+    n = 3000
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64)
+    vals = np.arange(n, dtype=np.uint32)
+    lk, lv = oracle.lsd_oop(keys, vals, n_t=4, sigma=256, bits=8, rounds=2)
+    P = _perm(keys, vals, b, p)
+    P.rounds(0, 2)
+    # cuts inside blocks, at block ends and starts, and the extremes
+    for m in sorted({n, n - 1, 2500, 17 * b + 1, 17 * b, 17 * b - 1, 5, 1, 0}, reverse=True):
+        P.truncate(m)
+        sk, sv = P.sequence()
+        assert len(P) == m
+        assert np.array_equal(sk, lk[:m]) and np.array_equal(sv, lv[:m]), m
+
+
+@pytest.mark.parametrize("b,p", [(4, 1), (16, 1), (64, 3), (8, 5)])
+def test_sort_after_truncate_and_finalize(b, p):
+    """The state after a truncation is a valid Radsort state (Sec. 4.1):
+    further rounds sort the truncated sequence stably, and Finalize puts it in
+    A; both equal the stable sort of the prefix computed by numpy."""
+    rng = np.random.default_rng(7 * b + p)
+    for trial in range(6):
+        n = int(rng.integers(200, 4000))
+        keys = rng.integers(0, 2 ** int(rng.integers(6, 33)), n, dtype=np.uint64)
+        vals = np.arange(n, dtype=np.uint32)
+        P = _perm(keys, vals, b, p)
+        r0 = int(rng.integers(0, 5))
+        P.rounds(0, r0)
+        m = int(rng.integers(0, n + 1))
+        P.truncate(m)
+        sk, sv = P.sequence()
+        P.rounds(0, 4)
+        fk, fv = P.sequence()
+        o = np.argsort(sk, kind="stable")
+        assert np.array_equal(fk, sk[o]) and np.array_equal(fv, sv[o])
+        k, v = P.finalize()
+        assert np.array_equal(k, fk) and np.array_equal(v, fv)
+
+
+def test_truncate_mutants():
+    """A stale P entry kept past the new end is caught by invariant 2 at once
+    (mutant 14); Finalize without the push of reading G16 writes a wrong
+    sequence on some truncated states (mutant 15) while the clean oracle never
+    does."""
+    keys = np.random.default_rng(3).integers(0, 2 ** 32, 3000, dtype=np.uint64)
+    vals = np.arange(3000, dtype=np.uint32)
+    P = _perm(keys, vals, 16, 3, mutant=14)
+    P.rounds(0, 2)
+    with pytest.raises(oracle.OracleError) as e:
+        P.truncate(1000)
+    assert e.value.code == -13
+    # small alphabets give few, long chains, where a remaining block sits in
+    # A block floor(n/b) behind other remaining blocks
+    rng = np.random.default_rng(9)
+    wrong = 0
+    for trial in range(400):
+        bits = int(rng.integers(1, 5))
+        n_t = 8
+        n = int(rng.integers(5, 300))
+        keys = rng.integers(0, 2 ** (bits * n_t), n, dtype=np.uint64)
+        vals = np.arange(n, dtype=np.uint32)
+        b, p = int(rng.choice([1, 2, 3, 4, 8])), int(rng.integers(1, 4))
+        m, r = int(rng.integers(1, n)), int(rng.integers(0, n_t + 1))
+        res = []
+        for mut in (0, 15):
+            P = oracle.Perm(keys, vals, n_t=n_t, sigma=1 << bits, bits=bits, b=b, p=p, mutant=mut)
+            P.rounds(0, r)
+            P.truncate(m)
+            sk, sv = P.sequence()
+            k, v = P.finalize()
+            res.append(np.array_equal(k, sk) and np.array_equal(v, sv))
+        assert res[0]
+        wrong += not res[1]
+    assert wrong > 0
