@@ -160,6 +160,71 @@ radsort_status radsort_sort_rounds(void *keys, uint32_t *values, size_t n, int k
                                    void *out_keys, uint32_t *out_values, void *stream);
 
 /*
+ * The permuted representation kept between calls (Sec. 4.1, "Avoiding
+ * Finalisation"; truncation is Alg. 8).  A handle holds a Radsort state on
+ * the caller's keys/values and workspace in the grid layout: the block map
+ * pi, whose logical blocks hold the current sequence, every block full but
+ * the last.  Rounds can be run on it, its blocks listed in logical order for
+ * consumers that only iterate (no data moves), the sequence cut to a prefix
+ * without disturbing the state, the data modified in place through the
+ * listed blocks and sorted again, and Finalize applied when the caller wants
+ * the sequence contiguous in keys/values.
+ *
+ * radsort_perm_workspace_size: device bytes the handle needs besides the
+ *   arrays (as radsort_workspace_size for the grid layout with block size
+ *   block_size, 0 = automatic).  EINVAL if the grid layout cannot take n
+ *   (n >= 2^31) or the block size is not one it takes.
+ * radsort_perm_open: setup (Alg. 4) on keys[0..n) / values (NULL = keys
+ *   only); the host handle is allocated with malloc and returned in *out.
+ *   keys, values and workspace stay in use until radsort_perm_close; their
+ *   contents are the state, not a sequence, until radsort_perm_finalize.
+ * radsort_perm_rounds: rounds first .. first+count-1 of Alg. 2's loop
+ *   (round r: sortPhase on digit n_t-1-r, i.e. bits [r*d, (r+1)*d) of the
+ *   key, then fixupPhase), 0 <= first, first + count <= n_t.  Rounds 0 ..
+ *   n_t-1 sort the current sequence completely; a later call may start over
+ *   at round 0 (after the keys were changed, or after a truncation).  The
+ *   digit histograms are taken from the current sequence when it changed
+ *   size since they were last taken; a caller who changed keys in place calls
+ *   radsort_perm_keys_changed first.
+ * radsort_perm_size: the current element count and the number of list
+ *   entries (floor(n/b) + 1; the last entry may have length 0).
+ * radsort_perm_blocks: writes the list to out_dev (device memory, at least
+ *   that many entries, else EINVAL): entry q is logical block q of the
+ *   sequence, with the device addresses of its first key and value and its
+ *   used length; the sequence is entry 0's elements, then entry 1's, ...
+ *   Valid until the next rounds / truncate / finalize call.
+ * radsort_perm_gather: copies the sequence into out_keys / out_values (n
+ *   entries each; out_values NULL = keys only).
+ * radsort_perm_truncate: keeps the first m <= n elements (Alg. 8); the
+ *   blocks past the new end become free blocks of the state.
+ * radsort_perm_finalize: Finalize (Alg. 7): keys[0..n) / values[0..n) then
+ *   hold the sequence; the handle accepts only radsort_perm_close after it.
+ * radsort_perm_close: frees the host handle (no device work, no wait).
+ * All calls but size and close are stream-ordered on `stream`.
+ */
+typedef struct radsort_perm radsort_perm;
+typedef struct {
+    uint64_t keys;     /* device address of the block's first key */
+    uint64_t values;   /* device address of its first value (0 without values) */
+    uint32_t len;      /* used elements, the block's keys[0 .. len) */
+    uint32_t reserved;
+} radsort_block;
+
+radsort_status radsort_perm_workspace_size(size_t n, int key_bytes, int value_bytes, int digit_bits,
+                                           uint32_t block_size, size_t *bytes);
+radsort_status radsort_perm_open(void *keys, uint32_t *values, size_t n, int key_bytes, int digit_bits,
+                                 uint32_t block_size, void *workspace, size_t workspace_bytes,
+                                 void *stream, radsort_perm **out);
+radsort_status radsort_perm_rounds(radsort_perm *h, int first, int count, void *stream);
+radsort_status radsort_perm_keys_changed(radsort_perm *h);
+radsort_status radsort_perm_size(const radsort_perm *h, size_t *n, size_t *entries);
+radsort_status radsort_perm_blocks(radsort_perm *h, radsort_block *out_dev, size_t cap, void *stream);
+radsort_status radsort_perm_gather(radsort_perm *h, void *out_keys, uint32_t *out_values, void *stream);
+radsort_status radsort_perm_truncate(radsort_perm *h, size_t m, void *stream);
+radsort_status radsort_perm_finalize(radsort_perm *h, void *stream);
+radsort_status radsort_perm_close(radsort_perm *h);
+
+/*
  * Comparison baseline: a conventional out-of-place LSD radix sort, Alg. 1
  * applied for t = n_t-1 .. 0, with one upfront pass that histograms all
  * digits and a decoupled look-back scan per round.  keys_alt / values_alt are

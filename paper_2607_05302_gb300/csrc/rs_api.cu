@@ -4,6 +4,7 @@
 // (Alg. 2).  Nothing here touches element data; every step runs in the
 // kernels of rs_round.cu and rs_finalize.cu.
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -1032,6 +1033,199 @@ radsort_status radsort_sort_rounds(void *keys, uint32_t *values, size_t n, int k
                        out_keys, out_values);
 }
 
+} // extern "C"
+
+// ---------------------------------------------------------------- permuted representation
+// Host handle of a Radsort state kept between calls (grid layout).  g0 is
+// the geometry of the array as opened (its block count npi never changes);
+// the current geometry has the current element count.
+struct radsort_perm {
+    Geom g0;
+    size_t n;          // current element count
+    Bufs w;
+    uint32_t *pc, *pn; // current and next block map
+    bool hist_ok;      // w.hist holds the current sequence's digit counts
+    bool finalized;
+};
+
+namespace {
+Geom perm_geom(const radsort_perm *h)
+{
+    Geom g = h->g0;
+    g.n = h->n;
+    g.nA = static_cast<uint32_t>(h->n / g.b);
+    return g; // npi, nT, H as opened
+}
+
+radsort_status perm_plan(size_t n, int kb, bool hasv, int db, uint32_t block_size, Geom *g)
+{
+    radsort_plan pl{};
+    pl.layout = RADSORT_LAYOUT_GRID;
+    pl.block_size = block_size;
+    return make_geom(n < 2 ? 2 : n, kb, hasv, db, &pl, g);
+}
+} // namespace
+
+extern "C" {
+
+radsort_status radsort_perm_workspace_size(size_t n, int key_bytes, int value_bytes, int digit_bits,
+                                           uint32_t block_size, size_t *bytes)
+{
+    if (!bytes || (value_bytes != 0 && value_bytes != 4))
+        return RADSORT_EINVAL;
+    *bytes = 0;
+    Geom g;
+    const radsort_status s = perm_plan(n, key_bytes, value_bytes == 4, digit_bits, block_size, &g);
+    if (s != RADSORT_OK)
+        return s;
+    g.n = n;
+    g.nA = static_cast<uint32_t>(n / g.b);
+    g.npi = g.nA + g.nT;
+    *bytes = layout(g, nullptr, nullptr);
+    return RADSORT_OK;
+}
+
+radsort_status radsort_perm_open(void *keys, uint32_t *values, size_t n, int key_bytes, int digit_bits,
+                                 uint32_t block_size, void *workspace, size_t workspace_bytes,
+                                 void *stream, radsort_perm **out)
+{
+    if (!out || !keys || !workspace || !aligned16(keys) || (values && !aligned16(values)) ||
+        !aligned16(workspace))
+        return RADSORT_EINVAL;
+    *out = nullptr;
+    Geom g;
+    radsort_status s = perm_plan(n, key_bytes, values != nullptr, digit_bits, block_size, &g);
+    if (s != RADSORT_OK)
+        return s;
+    g.n = n;
+    g.nA = static_cast<uint32_t>(n / g.b);
+    g.npi = g.nA + g.nT;
+    if (workspace_bytes < layout(g, nullptr, nullptr))
+        return RADSORT_ENOMEM;
+    radsort_perm *h = static_cast<radsort_perm *>(std::malloc(sizeof(radsort_perm)));
+    if (!h)
+        return RADSORT_ENOMEM;
+    h->g0 = g;
+    h->n = n;
+    layout(g, workspace, &h->w);
+    h->w.Ak = keys;
+    h->w.Av = values;
+    const size_t npi2 = g.npi + (g.npi & 1);
+    h->pc = h->w.aux;
+    h->pn = h->w.aux + npi2;
+    h->hist_ok = true; // setup takes the histograms of the input
+    h->finalized = false;
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e = cudaMemsetAsync(h->w.state, 0, ST_WORDS * 4, st);
+    if (e == cudaSuccess) {
+        Scope sc(0, -1, st);
+        e = launch_grid_setup(g, h->w, h->pc, st);
+    }
+    if (e != cudaSuccess) {
+        std::free(h);
+        return cuda_status(e);
+    }
+    *out = h;
+    return RADSORT_OK;
+}
+
+radsort_status radsort_perm_rounds(radsort_perm *h, int first, int count, void *stream)
+{
+    if (!h || h->finalized || first < 0 || count < 0 || first + count > h->g0.nt)
+        return RADSORT_EINVAL;
+    if (count == 0 || h->n <= 1)
+        return RADSORT_OK; // a sequence of at most one element is sorted
+    const Geom g = perm_geom(h);
+    cudaStream_t st = as_stream(stream);
+    // fresh tickets and an untagged look-back ring for this call's rounds
+    cudaError_t e = cudaMemsetAsync(h->w.ctr, 0, 64 * 4, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->w.status, 0, grid_ring_bytes(h->g0), st);
+    if (e == cudaSuccess && !h->hist_ok) {
+        Scope sc(0, -1, st);
+        e = launch_block_hist(g, h->w, h->pc, st);
+        if (e == cudaSuccess)
+            h->hist_ok = true;
+    }
+    for (int r = first; r < first + count && e == cudaSuccess; ++r) {
+        {
+            Scope sc(2, r, st);
+            e = launch_grid_prep(g, h->w, h->pc, h->pn, r, st);
+        }
+        if (e == cudaSuccess) {
+            Scope sc(1, r, st);
+            e = launch_grid_round(g, h->w, h->pc, h->pn, r, st);
+        }
+        std::swap(h->pc, h->pn);
+    }
+    return cuda_status(e);
+}
+
+radsort_status radsort_perm_keys_changed(radsort_perm *h)
+{
+    if (!h || h->finalized)
+        return RADSORT_EINVAL;
+    h->hist_ok = false;
+    return RADSORT_OK;
+}
+
+radsort_status radsort_perm_size(const radsort_perm *h, size_t *n, size_t *entries)
+{
+    if (!h)
+        return RADSORT_EINVAL;
+    if (n)
+        *n = h->n;
+    if (entries)
+        *entries = h->n / h->g0.b + 1;
+    return RADSORT_OK;
+}
+
+radsort_status radsort_perm_blocks(radsort_perm *h, radsort_block *out_dev, size_t cap, void *stream)
+{
+    if (!h || h->finalized || !out_dev || cap < h->n / h->g0.b + 1)
+        return RADSORT_EINVAL;
+    return cuda_status(launch_block_list(perm_geom(h), h->w, h->pc, out_dev, as_stream(stream)));
+}
+
+radsort_status radsort_perm_gather(radsort_perm *h, void *out_keys, uint32_t *out_values, void *stream)
+{
+    if (!h || h->finalized || (h->n && (!out_keys || !aligned16(out_keys))) ||
+        (out_values && !h->w.Av))
+        return RADSORT_EINVAL;
+    if (h->n == 0)
+        return RADSORT_OK;
+    const Geom g = perm_geom(h);
+    return cuda_status(launch_gather(g, h->w, h->pc, out_keys, out_values, as_stream(stream)));
+}
+
+radsort_status radsort_perm_truncate(radsort_perm *h, size_t m, void *stream)
+{
+    if (!h || h->finalized || m > h->n)
+        return RADSORT_EINVAL;
+    if (m == h->n)
+        return RADSORT_OK;
+    h->n = m;
+    h->hist_ok = false;
+    return cuda_status(launch_set_tail(perm_geom(h), h->w, as_stream(stream)));
+}
+
+radsort_status radsort_perm_finalize(radsort_perm *h, void *stream)
+{
+    if (!h || h->finalized)
+        return RADSORT_EINVAL;
+    h->finalized = true;
+    cudaStream_t st = as_stream(stream);
+    Scope sc(3, -1, st);
+    return cuda_status(launch_finalize(perm_geom(h), h->w, h->pc,
+                                       reinterpret_cast<unsigned long long *>(h->w.status), st));
+}
+
+radsort_status radsort_perm_close(radsort_perm *h)
+{
+    std::free(h);
+    return RADSORT_OK;
+}
+
 radsort_status radsort_float_keys(uint32_t *keys, size_t n, int inverse, void *stream)
 {
     if (n && !keys)
@@ -1075,7 +1269,8 @@ radsort_status radsort_device_status(void *stream)
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess)
         return cuda_status(e);
-    const unsigned v = take_status_round() | take_status_finalize() | take_status_oop() | take_status_seg();
+    const unsigned v = take_status_round() | take_status_finalize() | take_status_oop() | take_status_seg() |
+                       take_status_perm();
     if (v & ST_TIMEOUT)
         return RADSORT_ETIMEOUT;
     if (v & ST_INTERNAL)

@@ -255,7 +255,10 @@ __global__ void k_fz_chains(FinArgs a)
             h = x;
             r = hi32(a.jump[target_of(q, a.nA, a.nT)]);
         } else {
-            if (!(x < a.nT && x >= R))
+            // a path starts at a position no block moves into: a scratch
+            // block past the R targets in T or, after a truncation (Alg. 8),
+            // an A block at or past the first one that no block targets
+            if (!((x < a.nT && x >= R) || x >= a.nT + a.nA))
                 continue; // not a path start: some block moves into x
             const unsigned long long e = a.jump[x];
             h = lo32(e);

@@ -467,6 +467,11 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
         pin[i] = pi[NB + i];
     if (threadIdx.x == 0 && NB == nA)
         pin[H + nA] = pi[NB + H]; // the empty tail block
+    // the round reads free-list entries 0 .. H + nA only; blocks past them
+    // (free blocks left behind when the sequence was cut short, Alg. 8) keep
+    // their map entries
+    for (uint32_t i = H + nA + 1 + threadIdx.x; i < npi; i += blockDim.x)
+        pin[i] = pi[i];
 }
 
 // ---------------------------------------------------------------- round kernel

@@ -7,6 +7,8 @@
 #include <atomic>
 #include <mutex>
 
+#include "radsort.h"
+
 namespace rs {
 
 // bits of the device status words
@@ -145,5 +147,16 @@ extern std::atomic<unsigned long long> g_launches;
 unsigned take_status_round();
 unsigned take_status_finalize();
 unsigned take_status_oop();
+unsigned take_status_perm();
+
+// permuted representation kept between calls (grid layout; g.n is the
+// current element count, g.npi the block count of the original array)
+// digit histograms of the current sequence, read through pi
+cudaError_t launch_block_hist(const Geom &g, const Bufs &w, const uint32_t *pi, cudaStream_t st);
+// (key address, value address, length) of every logical block in order
+cudaError_t launch_block_list(const Geom &g, const Bufs &w, const uint32_t *pi, radsort_block *out,
+                              cudaStream_t st);
+// P and f after the sequence was cut to g.n elements (Alg. 8)
+cudaError_t launch_set_tail(const Geom &g, const Bufs &w, cudaStream_t st);
 
 } // namespace rs

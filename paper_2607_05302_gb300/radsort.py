@@ -75,6 +75,16 @@ def lib() -> ctypes.CDLL:
             "radsort_trace_enable": ([i], i),
             "radsort_trace_read": ([ctypes.POINTER(TraceRec), i, ctypes.POINTER(i)], i),
             "radsort_launch_count": ([ctypes.POINTER(ctypes.c_uint64)], i),
+            "radsort_perm_workspace_size": ([sz, i, i, i, u32, ctypes.POINTER(sz)], i),
+            "radsort_perm_open": ([vp, vp, sz, i, i, u32, vp, sz, vp, ctypes.POINTER(vp)], i),
+            "radsort_perm_rounds": ([vp, i, i, vp], i),
+            "radsort_perm_keys_changed": ([vp], i),
+            "radsort_perm_size": ([vp, ctypes.POINTER(sz), ctypes.POINTER(sz)], i),
+            "radsort_perm_blocks": ([vp, vp, sz, vp], i),
+            "radsort_perm_gather": ([vp, vp, vp, vp], i),
+            "radsort_perm_truncate": ([vp, sz, vp], i),
+            "radsort_perm_finalize": ([vp, vp], i),
+            "radsort_perm_close": ([vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -90,7 +100,9 @@ EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_autotune", "ra
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
            "radsort_lsd_oop_scratch_size", "radsort_float_keys",
            "radsort_device_status", "radsort_debug_wait_probe", "radsort_trace_enable", "radsort_trace_read",
-           "radsort_launch_count")
+           "radsort_launch_count", "radsort_perm_workspace_size", "radsort_perm_open", "radsort_perm_rounds",
+           "radsort_perm_keys_changed", "radsort_perm_size", "radsort_perm_blocks", "radsort_perm_gather",
+           "radsort_perm_truncate", "radsort_perm_finalize", "radsort_perm_close")
 
 
 def status_str(s: int) -> str:
@@ -283,3 +295,79 @@ def sort_segmented_tensors(keys, values, offsets_dev, offsets_host, *, digit_bit
 
 def float_keys_tensors(keys, inverse=False, stream=None):
     radsort_float_keys(_ptr(keys), keys.numel(), 1 if inverse else 0, _torch_stream(stream))
+
+
+# ---------------------------------------------------------------- permuted representation
+BLOCK_WORDS = 3  # radsort_block as three 64-bit words: keys address, values address, len | reserved << 32
+
+
+def perm_workspace_size(n, key_bytes, value_bytes, digit_bits=8, block_size=0):
+    out = ctypes.c_size_t(0)
+    _ok(lib().radsort_perm_workspace_size(n, key_bytes, value_bytes, digit_bits, block_size,
+                                          ctypes.byref(out)), "radsort_perm_workspace_size")
+    return int(out.value)
+
+
+class Perm:
+    """A Radsort state kept between calls on CUDA tensors (Sec. 4.1): rounds,
+    the block list in logical order, truncation (Alg. 8), the gathered
+    sequence and Finalize.  Every step runs in the CUDA library; this class
+    only marshals arguments."""
+
+    def __init__(self, keys, values=None, *, digit_bits=8, block_size=0, workspace=None, stream=None):
+        import torch
+
+        assert keys.is_cuda and keys.is_contiguous()
+        self.keys, self.values, self.digit_bits = keys, values, digit_bits
+        n = keys.numel()
+        need = perm_workspace_size(n, _key_bytes(keys), 4 if values is not None else 0, digit_bits,
+                                   block_size)
+        self.workspace = workspace if workspace is not None else torch.empty(
+            max(need, 1), dtype=torch.uint8, device=keys.device)
+        h = ctypes.c_void_p(0)
+        _ok(lib().radsort_perm_open(_ptr(keys), _ptr(values), n, _key_bytes(keys), digit_bits, block_size,
+                                    _ptr(self.workspace), self.workspace.numel(), _torch_stream(stream),
+                                    ctypes.byref(h)), "radsort_perm_open")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().radsort_perm_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rounds(self, first, count, stream=None):
+        _ok(lib().radsort_perm_rounds(self._h, first, count, _torch_stream(stream)), "radsort_perm_rounds")
+
+    def keys_changed(self):
+        _ok(lib().radsort_perm_keys_changed(self._h), "radsort_perm_keys_changed")
+
+    def size(self):
+        n, m = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _ok(lib().radsort_perm_size(self._h, ctypes.byref(n), ctypes.byref(m)), "radsort_perm_size")
+        return int(n.value), int(m.value)
+
+    def blocks(self, stream=None):
+        """The block list as an int64 CUDA tensor of shape (entries, 3):
+        key address, value address, used length."""
+        import torch
+
+        _, m = self.size()
+        out = torch.empty((m, BLOCK_WORDS), dtype=torch.int64, device=self.keys.device)
+        _ok(lib().radsort_perm_blocks(self._h, _ptr(out), m, _torch_stream(stream)), "radsort_perm_blocks")
+        return out
+
+    def gather(self, out_keys, out_values=None, stream=None):
+        _ok(lib().radsort_perm_gather(self._h, _ptr(out_keys), _ptr(out_values), _torch_stream(stream)),
+            "radsort_perm_gather")
+
+    def truncate(self, m, stream=None):
+        _ok(lib().radsort_perm_truncate(self._h, m, _torch_stream(stream)), "radsort_perm_truncate")
+
+    def finalize(self, stream=None):
+        _ok(lib().radsort_perm_finalize(self._h, _torch_stream(stream)), "radsort_perm_finalize")
