@@ -252,15 +252,17 @@ static cudaError_t launch_digit_hist(const void *keys, uint32_t n, int kb, int d
     return cudaGetLastError();
 }
 
-// Exclusive scan over an N-element array by a block of NT threads (each
-// thread a run of IPT consecutive elements); returns the total.  tmp: NT/32+1
-// words.  Ends with a barrier.
+// Exclusive scan over an N-element array by NT threads (each thread a run of
+// IPT consecutive elements); returns the total.  t: the caller's index among
+// the NT threads (whole warps: thread t is lane t % 32 of the group's warp
+// t / 32), bar: a barrier over exactly those threads.  tmp: NT/32+1 words.
+// Ends with a barrier.
 template <int N, int NT, typename F>
-__device__ __forceinline__ uint32_t block_scan(uint32_t *a, uint32_t *tmp, F &&bar)
+__device__ __forceinline__ uint32_t block_scan(uint32_t *a, uint32_t *tmp, F &&bar, int t)
 {
     constexpr int NWARP = NT / 32;
     constexpr int IPT = (N + NT - 1) / NT;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int lane = t & 31, w = t >> 5;
     uint32_t v[IPT], s = 0;
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -304,7 +306,7 @@ template <int DB> __global__ void __launch_bounds__(1024) k_offsets(const uint32
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x)
         s_a[c] = hist[r * SIGMA + c];
     __syncthreads();
-    block_scan<SIGMA, 1024>(s_a, s_tmp, [] { __syncthreads(); });
+    block_scan<SIGMA, 1024>(s_a, s_tmp, [] { __syncthreads(); }, threadIdx.x);
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x)
         off[r * (SIGMA + 1) + c] = s_a[c];
     if (threadIdx.x == 0)
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
             s_skip = 1;
     }
     __syncthreads();
-    block_scan<SIGMA, 1024>(s_O, s_tmp, bar);
+    block_scan<SIGMA, 1024>(s_O, s_tmp, bar, threadIdx.x);
     if (s_skip) {
         for (uint32_t i = threadIdx.x; i < npi; i += blockDim.x)
             pin[i] = pi[i];
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x)
         s_a[c] = inner(c) ? 1u : 0u;
     __syncthreads();
-    block_scan<SIGMA, 1024>(s_a, s_tmp, bar);
+    block_scan<SIGMA, 1024>(s_a, s_tmp, bar, threadIdx.x);
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x)
         if (inner(c))
             s_list[s_a[c]] = static_cast<uint32_t>(c);
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x, ++q)
         s_a[c] = fl[q];
     __syncthreads();
-    const uint32_t nS = block_scan<SIGMA, 1024>(s_a, s_tmp, bar);
+    const uint32_t nS = block_scan<SIGMA, 1024>(s_a, s_tmp, bar, threadIdx.x);
     q = 0;
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x, ++q)
         if (fl[q])
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x)
         s_a[c] = min(GRID_AHEAD, tns1[c] - tns0[c]);
     __syncthreads();
-    const uint32_t nF = block_scan<SIGMA, 1024>(s_a, s_tmp, bar);
+    const uint32_t nF = block_scan<SIGMA, 1024>(s_a, s_tmp, bar, threadIdx.x);
     for (int c = threadIdx.x; c < SIGMA; c += blockDim.x) {
         const uint32_t k = min(GRID_AHEAD, tns1[c] - tns0[c]);
         for (uint32_t i = 0; i < k; ++i)
@@ -475,26 +477,34 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
 }
 
 // ---------------------------------------------------------------- round kernel
-template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP> struct LbCfg {
+template <typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES, bool OOP> struct LbCfg {
     static constexpr int SIGMA = 1 << DB;
-    static constexpr int NT = NW * 32;       // consumer threads
-    static constexpr int THREADS = NT + 32;  // + one producer warp
+    // NG consumer groups of NW warps each; a group takes every NG-th tile and
+    // works through it on its own (its own named barrier, tables and lists),
+    // so the latency-bound phases of one group (look-back, block lists,
+    // stores) overlap the shared-memory-bound phases of another
+    static constexpr int NT = NW * 32;            // consumer threads per group
+    static constexpr int THREADS = NG * NT + 32;  // + one producer warp
     static constexpr int MAXM = TILE / 64;   // blocks per tile (b >= 64)
     static constexpr int R = TILE / NW;      // tile elements ranked per warp
     static constexpr int ITEMS = R / 32;     // elements per consumer thread
     static_assert(R % 32 == 0, "warp range must be a multiple of 32");
     static_assert(THREADS <= 1024, "one CTA holds at most 1024 threads");
+    // stage s serves group s % NG only: a group waits on the phases of its
+    // own stages, in order (a stage shared by two groups could let one group
+    // see an earlier phase of the other's fill as its own)
+    static_assert(STAGES % NG == 0, "stages split evenly between the groups");
     // threads per bucket in the column passes (each sums NW / TPB warp rows):
     // measured with 16 warps, one thread per bucket is fastest for sigma =
     // 256 (round 1.86 -> 1.83 ms at 2^28); for sigma = 2048 two were 5%
     // faster at 2^26 but at 2^30 u64 left some rounds 3x slower, four do not
-    static constexpr int TPB = NW >= 16 ? (DB <= 8 ? 1 : 4) : (NW >= 4 ? 2 : 1);
+    static constexpr int TPB = NW >= 16 ? (DB <= 8 ? 1 : 4) : (NT >= (1 << DB) ? 1 : 2);
     static_assert(NW % TPB == 0, "rows split evenly");
     // more than 16 elements per thread: digits are recomputed from the keys
     // and warp ranks kept as 16-bit halves, to stay within the registers
     static constexpr bool LEAN = ITEMS > 16;
     // CTAs per SM the configuration is built for (registers are capped to fit)
-    static constexpr int MINB = (NW <= 8 && DB <= 8) ? 2 : 1;
+    static constexpr int MINB = (NG * NW <= 8 && DB <= 8) ? 2 : 1;
     // sigma <= 256: a per-warp table of 32-bit lane masks by digit, built
     // with shared-memory atomicOr; sigma = 2048: one ballot per digit bit.
     // Either way a per-warp 16-bit row keeps the running count of each
@@ -511,25 +521,34 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP
     static constexpr size_t KBYTES = al(size_t(TILE) * sizeof(KT) + 16);
     static constexpr size_t STAGE = al(KBYTES + (HASV ? size_t(TILE) * 4 + 16 : 0));
     static constexpr size_t o_stage = 0;
-    static constexpr size_t o_hist = o_stage + STAGES * STAGE;
-    static constexpr size_t o_tab = o_hist + al(size_t(NW) * HROW * 2);
-    static constexpr size_t o_bk = o_tab + (PTAB ? al(size_t(NW) * 2 * SIGMA * 4) : 0);
-    // per bucket: tcnt, bstart, gpos, O (sigma + 1); with SMALL, Radsort adds
-    // the tables ns0, ns1, sh
-    static constexpr int NBK = (!OOP && SMALL) ? 7 : 4;
+    // per group: warp rows, mask tables, per-bucket words (tcnt, bstart,
+    // gpos), run offsets, block list, counters and scan scratch
+    static constexpr size_t HIST_BYTES = al(size_t(NW) * HROW * 2);
+    static constexpr size_t TAB_BYTES = PTAB ? al(size_t(NW) * 2 * SIGMA * 4) : 0;
+    static constexpr size_t BK_BYTES = al(size_t(3) * SIGMA * 4);
     // touched blocks per tile: at most TILE/b + 2 per bucket with elements
     static constexpr int LIST = MAXM + 2 * (SIGMA < TILE ? SIGMA : TILE) + 2;
     static constexpr size_t QB_BYTES = al(size_t(SIGMA) * 8);
     static constexpr size_t LK_BYTES = OOP ? 0 : al(size_t(LIST) * (SMALL ? 8 : 4));
     // sigma = 2048: the per-bucket run offsets and the block list live in
     // the warp-row region, which the tile no longer needs once reordered
-    static constexpr bool ALIAS = !SMALL && QB_BYTES + LK_BYTES <= size_t(NW) * HROW * 2;
-    static constexpr size_t o_qb = ALIAS ? o_hist : o_bk + al((size_t(NBK) * SIGMA + 4) * 4);
-    static constexpr size_t o_lk = o_qb + QB_BYTES;
-    static constexpr size_t o_meta = ALIAS ? o_bk + al((size_t(NBK) * SIGMA + 4) * 4) : o_lk + LK_BYTES;
+    static constexpr bool ALIAS = !SMALL && QB_BYTES + LK_BYTES <= HIST_BYTES;
+    static constexpr size_t MISC_BYTES = 512;
+    static constexpr size_t g_hist = 0;
+    static constexpr size_t g_tab = g_hist + HIST_BYTES;
+    static constexpr size_t g_bk = g_tab + TAB_BYTES;
+    static constexpr size_t g_qb = ALIAS ? g_hist : g_bk + BK_BYTES;
+    static constexpr size_t g_lk = g_qb + QB_BYTES;
+    static constexpr size_t g_misc = ALIAS ? g_bk + BK_BYTES : g_lk + LK_BYTES;
+    static constexpr size_t GROUP = al(g_misc + MISC_BYTES);
+    static constexpr size_t o_group = o_stage + STAGES * STAGE;
+    // shared by the groups (read only after the start): O (sigma + 1) and,
+    // with SMALL, Radsort's tables ns0, ns1, sh
+    static constexpr int NTAB = (!OOP && SMALL) ? 4 : 1;
+    static constexpr size_t o_tabs = o_group + NG * GROUP;
+    static constexpr size_t o_meta = o_tabs + al((size_t(NTAB) * SIGMA + 4) * 4);
     static constexpr size_t o_bar = o_meta + al(STAGES * 16);
-    static constexpr size_t o_misc = o_bar + al(2 * STAGES * 8);
-    static constexpr size_t SMEM = o_misc + 512;
+    static constexpr size_t SMEM = o_bar + al(2 * STAGES * 8);
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 
@@ -614,41 +633,44 @@ __device__ __forceinline__ uint32_t wait_pi(const uint32_t *p)
     return PI_NONE;
 }
 
-template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP>
-__global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::THREADS,
-                                   LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::MINB)
+template <typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES, bool OOP>
+__global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>::THREADS,
+                                   LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>::MINB)
     k_lb_round(LbArgs<KT> a)
 {
-    using C = LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>;
+    using C = LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>;
     constexpr int SIGMA = C::SIGMA, NT = C::NT;
     extern __shared__ __align__(128) unsigned char sm[];
     if (!OOP && a.state[ST_SKIP])
         return; // the digit is constant: the round is the identity
-    uint16_t *hist = reinterpret_cast<uint16_t *>(sm + C::o_hist);
-    unsigned *ptab = reinterpret_cast<unsigned *>(sm + C::o_tab);
-    uint32_t *bk = reinterpret_cast<uint32_t *>(sm + C::o_bk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // this warp's consumer group (the producer warp maps past the last one)
+    const int grp = warp / NW < NG ? warp / NW : 0;
+    unsigned char *gb = sm + C::o_group + size_t(grp) * C::GROUP;
+    uint16_t *hist = reinterpret_cast<uint16_t *>(gb + C::g_hist);
+    unsigned *ptab = reinterpret_cast<unsigned *>(gb + C::g_tab);
+    uint32_t *bk = reinterpret_cast<uint32_t *>(gb + C::g_bk);
     uint32_t *tcnt = bk, *bstart = bk + SIGMA, *gpos = bk + 2 * SIGMA;
-    uint32_t *sO = bk + 3 * SIGMA; // sigma + 1 entries
+    uint32_t *sO = reinterpret_cast<uint32_t *>(sm + C::o_tabs); // sigma + 1 entries
     uint32_t *stab = sO + SIGMA + 1;
     // bucket tables: shared memory (SMALL) or global
     const uint32_t *ns0 = C::SMALL ? stab : a.tab + SIGMA + 1;
     const uint32_t *ns1 = ns0 + SIGMA, *shr = ns1 + SIGMA;
-    uint2 *qb = reinterpret_cast<uint2 *>(sm + C::o_qb);
+    uint2 *qb = reinterpret_cast<uint2 *>(gb + C::g_qb);
     // list entries: the key block pointer tagged with its array (SMALL), or
     // the block index
-    unsigned long long *listk = reinterpret_cast<unsigned long long *>(sm + C::o_lk);
-    uint32_t *listb = reinterpret_cast<uint32_t *>(sm + C::o_lk);
+    unsigned long long *listk = reinterpret_cast<unsigned long long *>(gb + C::g_lk);
+    uint32_t *listb = reinterpret_cast<uint32_t *>(gb + C::g_lk);
     // byte distance from a key block to its value block, in T and in A
     const long long dvT = reinterpret_cast<const char *>(a.Tv) - reinterpret_cast<const char *>(a.Tk);
     const long long dvA = reinterpret_cast<const char *>(a.Av) - reinterpret_cast<const char *>(a.Ak);
     uint32_t *meta = reinterpret_cast<uint32_t *>(sm + C::o_meta);
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + C::o_bar);
     uint64_t *empty = full + STAGES;
-    // [0] consumed tiles, [1..3] a tile's list slots, blocks taken and blocks
-    // taken by earlier tiles, [8..] scan scratch
-    uint32_t *misc = reinterpret_cast<uint32_t *>(sm + C::o_misc);
+    // the group's [1..3] a tile's list slots, blocks taken and blocks taken
+    // by earlier tiles, [8..] scan scratch
+    uint32_t *misc = reinterpret_cast<uint32_t *>(gb + C::g_misc);
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t b = 1u << a.lb;
     const uint32_t mask = SIGMA - 1;
 
@@ -657,7 +679,6 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        misc[0] = 0;
         fence_mbar_init();
     }
     for (int c = tid; c <= SIGMA; c += C::THREADS)
@@ -667,8 +688,11 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             stab[c] = a.tab[SIGMA + 1 + c];
     }
     if constexpr (C::PTAB)
-        for (int i = tid; i < 2 * NW * SIGMA; i += C::THREADS)
-            ptab[i] = 0u;
+        for (int g = 0; g < NG; ++g) {
+            unsigned *pt = reinterpret_cast<unsigned *>(sm + C::o_group + size_t(g) * C::GROUP + C::g_tab);
+            for (int i = tid; i < 2 * NW * SIGMA; i += C::THREADS)
+                pt[i] = 0u;
+        }
     __syncthreads();
 
     auto kaddr = [&](uint32_t blk) -> KT * {
@@ -678,7 +702,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         return blk < a.nT ? a.Tv + (size_t(blk) << a.lb) : a.Av + (size_t(blk - a.nT) << a.lb);
     };
 
-    if (warp == NW) {
+    if (warp == NG * NW) {
         // ================================================================ producer
         uint32_t k = 0;
         uint32_t wm = 0; // tiles below wm have finished their look-back
@@ -713,11 +737,22 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 }
             }
             if (t >= a.ntiles) {
+                // every group stops at its next tile: NG end marks, each in
+                // the next stage in fill order
                 if (lane == 0) {
                     mt[0] = TILE_END;
                     mbar_arrive(&full[s]);
                 }
                 ++k;
+                bool ok = true;
+                for (int g = 1; g < NG && ok; ++g, ++k) {
+                    const int s2 = k % STAGES;
+                    ok = mbar_wait(&empty[s2], ((k / STAGES) & 1u) ^ 1u);
+                    if (ok && lane == 0) {
+                        meta[s2 * 4] = TILE_END;
+                        mbar_arrive(&full[s2]);
+                    }
+                }
                 break;
             }
             unsigned char *st = sm + C::o_stage + size_t(s) * C::STAGE;
@@ -816,12 +851,10 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 mbar_arrive(&full[s]); // release: the plain stores above are visible
         }
         // drain: every issued copy lands before this CTA exits (only the last
-        // STAGES issued tiles can still be in flight)
+        // STAGES fills can still be in flight, and no fill follows them, so
+        // the phase each of them completes stays readable)
         if (lane == 0) {
-            const uint32_t done = *(volatile uint32_t *)&misc[0];
-            uint32_t t0 = k > STAGES ? k - STAGES : 0;
-            if (done > t0)
-                t0 = done;
+            const uint32_t t0 = k > STAGES ? k - STAGES : 0;
             for (uint32_t t = t0; t < k; ++t)
                 mbar_wait(&full[t % STAGES], (t / STAGES) & 1u);
         }
@@ -829,22 +862,21 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
     }
 
     // ==================================================================== consumers
+    // thread and warp index within the group
+    const int ctid = tid - grp * NT, cw = warp - grp * NW;
     uint32_t *tmp = misc + 8;
-    auto bar = [] { named_bar(1, NT); };
+    auto bar = [grp] { named_bar(1 + grp, NT); };
     const uint32_t nP = OOP ? 0u : a.state[ST_NS]; // free-list entries taken before the round
     const uint32_t M = uint32_t(TILE) >> a.lb;
 
-    for (uint32_t k = 0;; ++k) {
+    for (uint32_t k = grp;; k += NG) { // fills grp, grp + NG, ...
         const int s = k % STAGES;
         if (!mbar_wait(&full[s], (k / STAGES) & 1u))
             break;
         const uint32_t *mt = meta + s * 4;
         const uint32_t t = mt[0];
-        if (t == TILE_END) {
-            if (tid == 0)
-                misc[0] = k + 1;
+        if (t == TILE_END)
             break;
-        }
         const uint32_t cnt = mt[1], leadk = mt[2], leadv = mt[3];
         unsigned char *st = sm + C::o_stage + size_t(s) * C::STAGE;
         KT *tk = reinterpret_cast<KT *>(st);
@@ -859,7 +891,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         // digit of item it (SIGMA past the tile's end) and its rank in the warp
         auto dig = [&](int it) -> uint32_t {
             if constexpr (C::LEAN)
-                return warp * C::R + it * 32 + lane < cnt ? digit_of(key[it], a.shift, mask)
+                return cw * C::R + it * 32 + lane < cnt ? digit_of(key[it], a.shift, mask)
                                                           : uint32_t(SIGMA);
             else
                 return digs[it];
@@ -878,7 +910,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         };
 #pragma unroll
         for (int it = 0; it < C::ITEMS; ++it) {
-            const uint32_t e = warp * C::R + it * 32 + lane;
+            const uint32_t e = cw * C::R + it * 32 + lane;
             key[it] = tk[leadk + e];
             if (HASV)
                 val[it] = tv[leadv + e];
@@ -886,7 +918,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 digs[it] = e < cnt ? digit_of(key[it], a.shift, mask) : uint32_t(SIGMA);
         }
         const unsigned lt = lanemask_lt();
-        uint16_t *hw = hist + warp * C::HROW;
+        uint16_t *hw = hist + cw * C::HROW;
         for (int c = lane; c < SIGMA; c += 32)
             hw[c] = 0;
         if constexpr (C::PTAB) {
@@ -896,7 +928,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             // the word.  Rows alternate between two mask tables, so the
             // clearing of one row and the ORs of the next never meet (a
             // table is all zero again two rows later)
-            unsigned *pt0 = ptab + warp * 2 * SIGMA;
+            unsigned *pt0 = ptab + cw * 2 * SIGMA;
             __syncwarp();
 #pragma unroll
             for (int it = 0; it < C::ITEMS; ++it) {
@@ -947,14 +979,14 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         }
         bar();
 
-        if (tid == 0) // this tile's slot counters (step 4)
+        if (ctid == 0) // this tile's slot counters (step 4)
             misc[1] = misc[2] = misc[3] = 0u;
 
         // ---- 2. tile counts per bucket, published for the look-back, and
         // their exclusive scan (bucket starts in the reordered tile)
         auto cnt_at = [&](int w, int c) -> uint32_t { return hist[w * C::HROW + c]; };
         constexpr int RPT = NW / C::TPB;
-        for (int i = tid; i < SIGMA * C::TPB; i += NT) {
+        for (int i = ctid; i < SIGMA * C::TPB; i += NT) {
             const int c = i / C::TPB, part = i % C::TPB;
             uint32_t sum = 0;
 #pragma unroll
@@ -971,10 +1003,10 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             }
         }
         bar();
-        block_scan<SIGMA, NT>(bstart, tmp, bar);
+        block_scan<SIGMA, NT>(bstart, tmp, bar, ctid);
         // each warp's start per bucket in the reordered tile: bucket start +
         // the counts of the warps before it (the ranks are warp-relative)
-        for (int i = tid; i < SIGMA * C::TPB; i += NT) {
+        for (int i = ctid; i < SIGMA * C::TPB; i += NT) {
             const int c = i / C::TPB, part = i % C::TPB;
             uint32_t h[RPT], sum = 0;
 #pragma unroll
@@ -1004,7 +1036,11 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         for (int it = 0; it < C::ITEMS; ++it) {
             const uint32_t d = dig(it);
             if (d < SIGMA) {
-                const uint32_t pos = cnt_at(warp, d) + get_rk(it);
+                const uint32_t pos = cnt_at(cw, d) + get_rk(it);
+                if (pos >= uint32_t(TILE)) { // only a broken scan gets here
+                    set_status(ST_INTERNAL);
+                    continue;
+                }
                 if constexpr (C::PAIR) {
                     tp[pos] = make_uint2(static_cast<uint32_t>(key[it]), val[it]);
                 } else {
@@ -1027,7 +1063,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         uint32_t pf[PFN], l0s[PFN], kos[PFN];
 #pragma unroll
         for (int q = 0; q < PFN; ++q) {
-            const int c = tid + q * NT;
+            const int c = ctid + q * NT;
             pf[q] = PI_NONE;
             l0s[q] = kos[q] = 0;
             if (c >= SIGMA) // whole warps: SIGMA and NT are multiples of 32
@@ -1044,6 +1080,13 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
                 qb[c] = make_uint2(g - bstart[c], 0u);
             } else {
                 gpos[c] = g;
+                // the run lies inside the bucket's output range unless the
+                // look-back words were corrupted: then it is reported and
+                // its blocks are left alone
+                const bool bad = g + cn > sO[c + 1] || g + cn < g;
+                if (bad)
+                    set_status(ST_INTERNAL);
+                const uint32_t cn = bad ? 0u : tcnt[c];
                 const uint32_t e = g + cn;
                 const uint32_t touched = cn ? ((e - 1) >> a.lb) - (g >> a.lb) + 1 : 0u;
                 const uint32_t cs = (g + b - 1) >> a.lb, ce = (e + b - 1) >> a.lb;
@@ -1074,7 +1117,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             }
         }
         bar();
-        if (tid == 0) // this tile reads no more look-back words
+        if (ctid == 0) // this tile reads no more look-back words
             st_volatile(a.done + (t & a.rmask), a.tagbase + t);
 
         uint32_t TT = 0; // list entries of this tile
@@ -1087,14 +1130,14 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
             const uint32_t fcap = min(a.H + (t + 1) * M, a.npi);
 #pragma unroll
             for (int q = 0; q < PFN; ++q) {
-                const int c = tid + q * NT;
+                const int c = ctid + q * NT;
                 if (c >= SIGMA)
                     continue;
                 const uint32_t g = gpos[c], cn = tcnt[c];
                 const uint32_t l0 = l0s[q], j0 = g >> a.lb;
                 qb[c] = make_uint2(g - bstart[c], l0 - j0);
-                if (!cn)
-                    continue;
+                if (!cn || g + cn > sO[c + 1] || g + cn < g)
+                    continue; // (a corrupted run was reported in step 4)
                 const uint32_t touched = ((g + cn - 1) >> a.lb) - j0 + 1;
                 const uint32_t n0 = ns0[c], n1 = ns1[c];
                 const uint32_t cs = (g + b - 1) >> a.lb, ce = (g + cn + b - 1) >> a.lb;
@@ -1147,7 +1190,7 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         constexpr int SI = (TILE + NT - 1) / NT;
 #pragma unroll 4
         for (int kk = 0; kk < SI; ++kk) {
-            const uint32_t i = tid + kk * NT;
+            const uint32_t i = ctid + kk * NT;
             if (i < cnt) {
                 KT kv;
                 uint32_t vv = 0;
@@ -1199,24 +1242,24 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>::TH
         // producer refills it with bulk copies (async proxy)
         fence_proxy_async_smem();
         bar();
-        if (tid == 0)
+        if (ctid == 0)
             mbar_arrive(&empty[s]); // stage consumed: the producer may refill it
     }
 }
 
 // ---------------------------------------------------------------- launch helpers
-template <typename KT, bool HASV, int DB, int TILE, int NW, int STAGES, bool OOP>
+template <typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES, bool OOP>
 static int lb_ctas(size_t ntiles)
 {
-    using C = LbCfg<KT, HASV, DB, TILE, NW, STAGES, OOP>;
+    using C = LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>;
     static DeviceOnce attr; // per template instance
     if (attr.run([] {
-            return cudaFuncSetAttribute(k_lb_round<KT, HASV, DB, TILE, NW, STAGES, OOP>,
+            return cudaFuncSetAttribute(k_lb_round<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
         }) != cudaSuccess)
         return -1;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_round<KT, HASV, DB, TILE, NW, STAGES, OOP>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lb_round<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>,
                                                   C::THREADS, C::SMEM);
     if (per_sm < 1)
         per_sm = 1;
@@ -1226,26 +1269,34 @@ static int lb_ctas(size_t ntiles)
     return grid < 1 ? 1 : static_cast<int>(grid);
 }
 
-// Calls f.template operator()<KT, HASV, DB, TILE, NW, STAGES>() for the configuration.
+// Calls f.template operator()<KT, HASV, DB, TILE, NW, NG, STAGES>() for the configuration.
 template <typename F> static cudaError_t lb_dispatch(int kb, int db, bool hasv, F &&f)
 {
     using u64 = unsigned long long;
     // The largest tiles that two stages and the tables leave room for
     // (per-tile costs scale with sigma, not with the tile), each a multiple
     // of 2048 so that blocks of up to 2048 elements fit whole; 11-bit digits
-    // keep their run offsets and block list in the warp rows (ALIAS)
+    // keep their run offsets and block list in the warp rows (ALIAS).
+    // One group of 16 consumer warps and two stages throughout.  Measured at
+    // 2^30 u32 keys + values, 8-bit digits (round kernel): tiles of 10240,
+    // 7.29 ms; tiles of 4096, 10.7 ms; two groups of 8 warps on tiles of
+    // 4096 with two stages each, 8.21 ms; two groups on 8192 / 6144 with one
+    // stage each, 9.34 / 9.93 ms.  Per-tile work over the sigma buckets
+    // (column sums, scan, look-back, block lists) costs about 6800 cycles a
+    // tile whatever its size, so the largest tile wins even though a second
+    // group overlaps some of it.
     if (kb == 4) {
         if (db == 8)
-            return hasv ? f.template operator()<uint32_t, true, 8, 10240, 16, 2>()
-                        : f.template operator()<uint32_t, false, 8, 16384, 16, 2>();
-        return hasv ? f.template operator()<uint32_t, true, 11, 8192, 16, 2>()
-                    : f.template operator()<uint32_t, false, 11, 16384, 16, 2>();
+            return hasv ? f.template operator()<uint32_t, true, 8, 10240, 16, 1, 2>()
+                        : f.template operator()<uint32_t, false, 8, 16384, 16, 1, 2>();
+        return hasv ? f.template operator()<uint32_t, true, 11, 8192, 16, 1, 2>()
+                    : f.template operator()<uint32_t, false, 11, 16384, 16, 1, 2>();
     }
     if (db == 8)
-        return hasv ? f.template operator()<u64, true, 8, 6144, 16, 2>()
-                    : f.template operator()<u64, false, 8, 10240, 16, 2>();
-    return hasv ? f.template operator()<u64, true, 11, 4096, 16, 2>()
-                : f.template operator()<u64, false, 11, 8192, 16, 2>();
+        return hasv ? f.template operator()<u64, true, 8, 6144, 16, 1, 2>()
+                    : f.template operator()<u64, false, 8, 10240, 16, 1, 2>();
+    return hasv ? f.template operator()<u64, true, 11, 4096, 16, 1, 2>()
+                : f.template operator()<u64, false, 11, 8192, 16, 1, 2>();
 }
 
 } // namespace
@@ -1253,7 +1304,7 @@ template <typename F> static cudaError_t lb_dispatch(int kb, int db, bool hasv, 
 uint32_t lb_tile(int kb, int db, bool hasv)
 {
     uint32_t r = 0;
-    lb_dispatch(kb, db, hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int STAGES>() {
+    lb_dispatch(kb, db, hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
         r = TILE;
         return cudaSuccess;
     });
@@ -1261,15 +1312,20 @@ uint32_t lb_tile(int kb, int db, bool hasv)
 }
 
 // ---------------------------------------------------------------- look-back ring
-// Rows of the look-back ring: a power of two, no more than the tiles, at most
-// 4096 rows (sigma = 256) or 1024 (sigma = 2048): a few MB whatever n.
+// Rows of the look-back ring: a power of two, no more than the tiles' power
+// of two up to 512 rows, a quarter of it beyond (the tiles in flight at once,
+// at most STAGES per SM, mostly fit; a tile whose slot is still in use waits
+// for it), at most 2048 rows (sigma = 256) or 1024 (sigma = 2048): a few MB
+// whatever n.
 static uint32_t ring_rows(size_t ntiles, uint32_t sigma)
 {
-    const uint32_t cap = sigma <= 256 ? 4096u : 1024u;
+    const uint32_t cap = sigma <= 256 ? 2048u : 1024u;
     uint32_t r = 1;
-    while (r < ntiles && r < cap)
+    while (r < ntiles && r < 4 * cap)
         r <<= 1;
-    return r;
+    if (r > 512)
+        r = r / 4 > 512 ? r / 4 : 512u;
+    return r < cap ? r : cap;
 }
 
 static size_t ring_bytes(size_t ntiles, uint32_t sigma)
@@ -1335,10 +1391,10 @@ cudaError_t launch_grid_round(const Geom &g, const Bufs &w, const uint32_t *pi, 
                               int round, cudaStream_t st)
 {
     const uint32_t n = static_cast<uint32_t>(g.n);
-    return lb_dispatch(g.kb, g.db, g.hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int STAGES>() {
-        using C = LbCfg<KT, HASV, DB, TILE, NW, STAGES, false>;
+    return lb_dispatch(g.kb, g.db, g.hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
+        using C = LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, false>;
         const size_t ntiles = (g.n + TILE - 1) / TILE;
-        const int grid = lb_ctas<KT, HASV, DB, TILE, NW, STAGES, false>(ntiles);
+        const int grid = lb_ctas<KT, HASV, DB, TILE, NW, NG, STAGES, false>(ntiles);
         if (grid < 0)
             return cudaErrorInvalidValue;
         LbArgs<KT> a{};
@@ -1363,7 +1419,7 @@ cudaError_t launch_grid_round(const Geom &g, const Bufs &w, const uint32_t *pi, 
         a.npi = g.npi;
         a.lb = g.lb;
         a.shift = static_cast<uint32_t>(round * g.db);
-        k_lb_round<KT, HASV, DB, TILE, NW, STAGES, false><<<grid, C::THREADS, C::SMEM, st>>>(a);
+        k_lb_round<KT, HASV, DB, TILE, NW, NG, STAGES, false><<<grid, C::THREADS, C::SMEM, st>>>(a);
         g_launches += 1;
         return cudaGetLastError();
     });
@@ -1419,9 +1475,9 @@ cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32
         g_launches += 1;
     }
     if (e == cudaSuccess)
-        e = lb_dispatch(kb, db, vals != nullptr, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int STAGES>() {
-        using C = LbCfg<KT, HASV, DB, TILE, NW, STAGES, true>;
-        const int grid = lb_ctas<KT, HASV, DB, TILE, NW, STAGES, true>(ntiles);
+        e = lb_dispatch(kb, db, vals != nullptr, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
+        using C = LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, true>;
+        const int grid = lb_ctas<KT, HASV, DB, TILE, NW, NG, STAGES, true>(ntiles);
         if (grid < 0)
             return cudaErrorInvalidValue;
         KT *src = static_cast<KT *>(keys), *dst = static_cast<KT *>(keys_alt);
@@ -1441,7 +1497,7 @@ cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32
             a.n = nn;
             a.ntiles = static_cast<uint32_t>(ntiles);
             a.shift = static_cast<uint32_t>(r * DB);
-            k_lb_round<KT, HASV, DB, TILE, NW, STAGES, true><<<grid, C::THREADS, C::SMEM, st>>>(a);
+            k_lb_round<KT, HASV, DB, TILE, NW, NG, STAGES, true><<<grid, C::THREADS, C::SMEM, st>>>(a);
             g_launches += 1;
             std::swap(src, dst);
             std::swap(vs, vd);
