@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--block-size", type=int, default=0)
     ap.add_argument("--num-chunks", type=int, default=0)
-    ap.add_argument("--layout", default="auto", choices=["auto", "grid", "chunks"],
-                    help="block layout (auto: the automatic plan, the grid layout below 2^31)")
+    ap.add_argument("--layout", default="auto", choices=["auto", "grid", "chunks", "msd"],
+                    help="block layout (auto: the automatic plan, the grid layout below 2^31; msd: the "
+                         "MSD split of Sec. 4.3)")
     ap.add_argument("--no-oop", action="store_true", help="skip the out-of-place comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
@@ -408,7 +409,7 @@ def run_segmented(a):
     }), flush=True)
 
 
-def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream):
+def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream, layout=0, with_oop=True):
     """One more single-array workload (uniform keys, index payload): Radsort
     in the automatic plan and the out-of-place comparator on the same data,
     each timed over `steps` fresh copies with CUDA events; the round kernel's
@@ -421,8 +422,11 @@ def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream):
     keys0 = ((r >> 32) & 0xFFFFFFFF).to(torch.int64).to(torch.int32) if kb == 4 else r
     del r
     vals0 = torch.arange(n, dtype=torch.int32, device=dev)
-    bs, pc, lay = R.radsort_plan_default(n, kb, 4, db)
-    wsb = R.radsort_workspace_size(n, kb, 4, db)
+    if layout:
+        bs, pc, lay = 0, 0, layout
+    else:
+        bs, pc, lay = R.radsort_plan_default(n, kb, 4, db)
+    wsb = R.radsort_workspace_size(n, kb, 4, db, 0, 0, layout)
     ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
     free_b = torch.cuda.mem_get_info(dev)[0]
     nbuf = int(max(2, min(steps + warmup, (free_b * 0.4) // (n * E))))
@@ -455,7 +459,7 @@ def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream):
 
     R.radsort_trace_read()
     R.radsort_trace_enable(True)
-    ms = run(lambda i: R.sort_tensors(kbufs[i], vbufs[i], digit_bits=db, workspace=ws))
+    ms = run(lambda i: R.sort_tensors(kbufs[i], vbufs[i], digit_bits=db, workspace=ws, layout=layout))
     R.radsort_trace_enable(False)
     recs = R.radsort_trace_read()
     # the last step's result: sorted and a stable permutation of the input
@@ -470,23 +474,28 @@ def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream):
     fin = [t for ph, rd, t in recs if ph == "Finalize"]
     avg_round = statistics.mean(rounds) if rounds else float("nan")
     hbm, src = peaks()
-    ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
-    oms = run(lambda i: R.lsd_oop_tensors(kbufs[i], vbufs[i], ka, va, digit_bits=db))
     val = n / (ms / 1e3) / 1e9
-    oval = n / (oms / 1e3) / 1e9
+    oms = oval = None
+    if with_oop:
+        ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
+        oms = run(lambda i: R.lsd_oop_tensors(kbufs[i], vbufs[i], ka, va, digit_bits=db))
+        oval = n / (oms / 1e3) / 1e9
+        del ka, va
     out = {
-        "workload": f"radsort_{'u32' if kb == 4 else 'u64'}_keys_u32_index_2^{log2n}_uniform_d{db}",
+        "workload": f"radsort_{'u32' if kb == 4 else 'u64'}_keys_u32_index_2^{log2n}_uniform_d{db}"
+                    + (f"_{layout}" if layout else ""),
         "n": n, "value": round(val, 3), "unit": "Gkeys/s", "ms_per_step": round(ms, 3), "steps": steps,
         "block_size": bs, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
         "round_ms": round(avg_round, 4),
         "round_frac": round((n * 2 * E) / (avg_round / 1e3) / 1e9 / hbm, 4),
         "finalize_ms": round(statistics.mean(fin), 4) if fin else None,
         "result_checked": ok,
-        "oop": {"value": round(oval, 3), "ms_per_step": round(oms, 3),
-                "extra_bytes": n * E + R.radsort_lsd_oop_scratch_size(n, kb, 4, db)},
-        "radsort_over_oop": round(val / oval, 4),
+        "oop": None if oval is None else {
+            "value": round(oval, 3), "ms_per_step": round(oms, 3),
+            "extra_bytes": n * E + R.radsort_lsd_oop_scratch_size(n, kb, 4, db)},
+        "radsort_over_oop": None if oval is None else round(val / oval, 4),
     }
-    del kbufs, vbufs, ws, ka, va, keys0, vals0
+    del kbufs, vbufs, ws, keys0, vals0
     torch.cuda.empty_cache()
     return out
 
@@ -557,7 +566,7 @@ def main():
     else:
         bs, pc = a.block_size, 0
     wsb = R.radsort_workspace_size(n, kb, 4, db, bs, pc, lay)
-    if not bs:
+    if not bs and lay != "msd":
         bs, _, _ = R.radsort_plan_default(n, kb, 4, db)
     ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
 
@@ -710,6 +719,11 @@ def main():
             key = f"{'u32' if kb2 == 4 else 'u64'}_2^{lg}_d{db2}"
             extra[key] = time_workload(R, W, dev, lg, kb2, db2, min(a.steps, 6), max(3, min(a.warmup, 3)),
                                        barrier, stream)
+        # the MSD split of Sec. 4.3 on the headline workload (its comparator
+        # is the line's own oop)
+        extra[f"msd_split_{'u32' if kb == 4 else 'u64'}_2^{a.log2n}_d{db}"] = (
+            time_workload(R, W, dev, a.log2n, kb, db, min(a.steps, 6), max(3, min(a.warmup, 3)), barrier,
+                          stream, layout="msd", with_oop=False) if db == 8 else None)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -62,6 +62,14 @@ typedef enum {
  *    by the buckets in them).  All SMs work on it through a decoupled
  *    look-back; T holds 4*sigma + 1 blocks whatever the parallelism, and
  *    after the last round every block but the tail is full.  Needs n < 2^31.
+ *  RADSORT_LAYOUT_MSD: the MSD split of Sec. 4.3 (last paragraph): the first
+ *    round sorts by the most significant digit in the chunk layout with
+ *    p = sigma chunks, its sigma buckets become the chunks, and every chunk
+ *    then runs the remaining rounds from its least significant digit on its
+ *    own (each CTA's working set is one bucket).  8-bit digits only (T holds
+ *    2*sigma^2 blocks); num_chunks must be 0; block_size 0 picks the largest
+ *    of 64 .. 1024 within 2% of the array (else 64).  With radsort_sort_rounds,
+ *    round 1 is the split and round r > 1 the digit at bits [(r-2)*8, (r-1)*8).
  *  RADSORT_LAYOUT_SCRATCH: short arrays are sorted out of place (Alg. 1) with
  *    the alternate arrays inside the workspace, the paper's suggestion for
  *    arrays below Radsort's crossover (Sec. 5: use T as A').  The automatic
@@ -72,6 +80,7 @@ typedef enum {
 #define RADSORT_LAYOUT_CHUNKS 1u
 #define RADSORT_LAYOUT_GRID 2u
 #define RADSORT_LAYOUT_SCRATCH 3u
+#define RADSORT_LAYOUT_MSD 4u
 #define RADSORT_SCRATCH_MAX_N ((size_t)1 << 18)
 
 /* Tuning plan.  Zero fields mean "choose automatically": the scratch layout

@@ -227,3 +227,37 @@ class Perm:
         st = Stats()
         self._lib.ora_perm_stats(self._h, ctypes.byref(st))
         return st.as_dict()
+
+
+def msd_split(keys, vals=None, *, n_t, sigma, bits, b, rounds=None):
+    """The MSD split suggested for parallel operation (Sec. 4.3, last
+    paragraph): one round on the most significant digit splits the input into
+    sigma buckets, then each bucket is sorted on its own by the remaining
+    digits from the least significant one.  Returns the sequence after
+    `rounds` rounds (default n_t): round 1 is the split, round r > 1 the
+    (r-1)-th least significant digit inside every bucket.  Both steps are this
+    oracle's Radsort (Alg. 2-6, p = 1): the split is one round on the keys'
+    top digit, each bucket's sort the first rounds-1 rounds on its keys."""
+    k, v = _prep(keys, vals)
+    r = n_t if rounds is None else rounds
+    if r == 0 or k.size == 0:
+        return k, v
+    shift = np.uint64((n_t - 1) * bits) if bits > 0 else None
+    top = (k >> shift) & np.uint64(sigma - 1) if bits > 0 else k // np.uint64(sigma ** (n_t - 1)) % np.uint64(sigma)
+    pos = np.arange(k.size, dtype=np.uint32)
+    _, order = radsort(top, pos, n_t=1, sigma=sigma, bits=bits, b=b, p=1)
+    k, v = k[order], (None if v is None else v[order])
+    if r == 1:
+        return k, v
+    tops = top[order]
+    starts = np.flatnonzero(np.r_[True, tops[1:] != tops[:-1]])
+    ends = np.r_[starts[1:], k.size]
+    out_k, out_v = k.copy(), (None if v is None else v.copy())
+    for s0, s1 in zip(starts, ends):
+        idx = np.arange(s1 - s0, dtype=np.uint32)
+        sk, si = radsort(k[s0:s1], idx, n_t=n_t, sigma=sigma, bits=bits, b=b, p=1, rounds=r - 1,
+                         finalize=False)
+        out_k[s0:s1] = sk
+        if v is not None:
+            out_v[s0:s1] = v[s0:s1][si]
+    return out_k, out_v

@@ -142,6 +142,7 @@ static radsort_status fill_geom(size_t n, int kb, bool hasv, int db, uint32_t b,
     g->npi = static_cast<uint32_t>(npi);
     g->G = static_cast<uint32_t>(H);
     g->grid = false;
+    g->msd = false;
     return RADSORT_OK;
 }
 
@@ -164,6 +165,7 @@ static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32
     g->lb = ilog2(b);
     g->p = 1;
     g->grid = true;
+    g->msd = false;
     const unsigned long long nA = n / b;
     const unsigned long long H = (GRID_AHEAD + 2ull) * g->sigma;
     const unsigned long long npi = nA + H + 1;
@@ -266,13 +268,46 @@ static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl)
     pl->num_chunks = best_p;
 }
 
+// MSD split, then every bucket on its own (Sec. 4.3, last paragraph): the
+// chunk layout with one chunk per bucket of the top digit, p = sigma (8-bit
+// digits: T holds 2*sigma^2 blocks).  Block size: the plan's, else the
+// largest in 64 .. 1024 whose workspace is within 2% of the array's bytes,
+// else the smallest the block indices allow.
+static radsort_status make_geom_msd(size_t n, int kb, bool hasv, int db, uint32_t b, Geom *g)
+{
+    if (db != 8)
+        return RADSORT_EINVAL;
+    const uint32_t sigma = 1u << db;
+    if (!b) {
+        uint32_t within = 0, valid = 0;
+        for (uint32_t cb = 64; cb <= 1024; cb *= 2) {
+            Geom t;
+            if (fill_geom(n, kb, hasv, db, cb, sigma, &t) != RADSORT_OK)
+                continue;
+            if (!valid)
+                valid = cb;
+            if (double(layout(t, nullptr, nullptr)) <= 0.02 * double(n) * double(kb + (hasv ? 4 : 0)))
+                within = cb;
+        }
+        b = within ? within : valid;
+        if (!b)
+            return RADSORT_EINVAL;
+    }
+    const radsort_status s = fill_geom(n, kb, hasv, db, b, sigma, g);
+    if (s == RADSORT_OK)
+        g->msd = true;
+    return s;
+}
+
 static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radsort_plan *plan,
                                 Geom *g)
 {
     if ((kb != 4 && kb != 8) || (db != 8 && db != 11))
         return RADSORT_EINVAL;
-    if (plan && plan->layout > RADSORT_LAYOUT_SCRATCH)
+    if (plan && plan->layout > RADSORT_LAYOUT_MSD)
         return RADSORT_EINVAL;
+    if (plan && plan->layout == RADSORT_LAYOUT_MSD)
+        return plan->num_chunks ? RADSORT_EINVAL : make_geom_msd(n, kb, hasv, db, plan->block_size, g);
     radsort_plan pl{};
     if (plan && plan->layout != RADSORT_LAYOUT_SCRATCH)
         pl.layout = plan->layout;
@@ -419,13 +454,22 @@ static cudaError_t run_rounds(const Geom &g, Bufs &w, int rounds, cudaStream_t s
         e = launch_setup(g, w, pc, st);
     }
     for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+        // digit of round r and the order of its output: least significant
+        // first across all chunks; with the MSD split, the top digit first
+        // (its buckets become the chunks), then each chunk on its own from
+        // its least significant digit
+        int pos = r, mode = FIX_EVEN;
+        if (g.msd) {
+            pos = r == 0 ? g.nt - 1 : r - 1;
+            mode = r == 0 ? FIX_SPLIT : FIX_PER_CHUNK;
+        }
         {
-            Scope sc(1, r, st);
-            e = launch_round(g, w, pc, lc, UC, r, st);
+            Scope sc(1, pos, st);
+            e = launch_round(g, w, pc, lc, UC, pos, st);
         }
         if (e == cudaSuccess) {
-            Scope sc(2, r, st);
-            e = launch_fixup(g, w, pc, pn, UC, lc, ln, st);
+            Scope sc(2, pos, st);
+            e = launch_fixup(g, w, pc, pn, UC, lc, ln, mode, st);
         }
         uint32_t *t = pc;
         pc = pn;

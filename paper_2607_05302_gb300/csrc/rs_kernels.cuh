@@ -30,6 +30,7 @@ struct Geom {
     uint32_t npi;      // nA + nT
     uint32_t G;        // groups (bucket, chunk) = sigma*p
     bool grid;         // one chain per bucket on the output block grid (H = (GRID_AHEAD + 2) sigma, nT = H + 1)
+    bool msd;          // chunk layout with p = sigma: a split on the top digit, then each bucket on its own
 };
 
 // Device buffers of one sort, carved from one workspace allocation.
@@ -65,12 +66,14 @@ enum { ST_F = 0, ST_NP = 1, ST_FPREV = 2, ST_LOFFTOT = 3, ST_NS = 4, ST_SKIP = 5
 
 // setup (Alg. 4) + chunk bounds of round 0
 cudaError_t launch_setup(const Geom &g, const Bufs &w, uint32_t *pi, cudaStream_t st);
-// one sortPhase (Alg. 5) over p chunks
+// one sortPhase (Alg. 5) over p chunks on the digit at bits [pos*d, (pos+1)*d)
 cudaError_t launch_round(const Geom &g, const Bufs &w, const uint32_t *pi, const uint32_t *lo,
-                         uint32_t *UC, int round, cudaStream_t st);
-// fixupPhase (Alg. 6): scan + placement into pi_new
+                         uint32_t *UC, int pos, cudaStream_t st);
+// fixupPhase (Alg. 6): scan + placement into pi_new; the group order and the
+// next chunk bounds by mode
+enum FixMode { FIX_EVEN = 0, FIX_SPLIT = 1, FIX_PER_CHUNK = 2 };
 cudaError_t launch_fixup(const Geom &g, const Bufs &w, const uint32_t *pi_old, uint32_t *pi_new,
-                         const uint32_t *UC, const uint32_t *lo_old, uint32_t *lo_new,
+                         const uint32_t *UC, const uint32_t *lo_old, uint32_t *lo_new, int mode,
                          cudaStream_t st);
 // grid layout: digit histograms + setup; per round the tables and the
 // prefilled next map (prep), then sortPhase

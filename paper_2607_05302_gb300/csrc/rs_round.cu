@@ -702,9 +702,17 @@ cudaError_t launch_round(const Geom &g, const Bufs &w, const uint32_t *pi, const
 }
 
 // ====================================================================== fixupPhase
-// One CTA: scans over the sigma*p groups (bucket-major, chunk-minor, which
-// keeps equal digits of earlier chunks first: stability across chunks), the
-// new P, f, the leftover offsets and the chunk bounds of the next round.
+// One CTA: scans over the sigma*p groups, the new P, f, the leftover offsets
+// and the chunk bounds of the next round.  Group (bucket c, chunk q) is
+// C[c*p + q].  Modes (FixMode):
+//   EVEN: bucket-major, chunk-minor order (equal digits of earlier chunks
+//     first: stability across chunks, Sec. 4.3); the next round's chunks
+//     split the elements evenly;
+//   SPLIT: the same order, and the next round's chunk q is bucket q (an MSD
+//     split, Sec. 4.3: p = sigma);
+//   PER_CHUNK: chunk-major, bucket-minor order: each chunk's output stays a
+//     run of its own (the chunk is sorted independently), and the next
+//     round's chunks are the same runs.
 constexpr int FX_T = 1024;
 
 // exclusive scan over a 1024-thread block; s_w holds 33 entries
@@ -735,17 +743,22 @@ __global__ void __launch_bounds__(FX_T) k_fixup_scan(const uint32_t *C, const ui
                                                       uint32_t *lo_new, uint32_t *LOff,
                                                       uint32_t *state, uint32_t G, uint32_t p,
                                                       uint32_t sigma, uint32_t H, uint32_t npi,
-                                                      uint32_t b, unsigned long long n)
+                                                      uint32_t b, unsigned long long n, int mode)
 {
     __shared__ unsigned long long s_e[33];
     __shared__ uint32_t s_c[33];
     const int t = threadIdx.x;
+    // group of position i in the order of the output
+    auto grp = [&](uint32_t i) -> uint32_t {
+        return mode == FIX_PER_CHUNK ? (i % sigma) * p + i / sigma : i;
+    };
     // groups: block counts and element counts
     const uint32_t per = (G + FX_T - 1) / FX_T;
     const uint32_t g0 = min(G, t * per), g1 = min(G, g0 + per);
     uint32_t sc = 0;
     unsigned long long se = 0;
-    for (uint32_t g = g0; g < g1; ++g) {
+    for (uint32_t i = g0; i < g1; ++i) {
+        const uint32_t g = grp(i);
         sc += C[g];
         se += (unsigned long long)(C[g] - 1) * b + FILL[g];
     }
@@ -753,11 +766,12 @@ __global__ void __launch_bounds__(FX_T) k_fixup_scan(const uint32_t *C, const ui
     unsigned long long totE;
     uint32_t ec = block_excl_scan<uint32_t>(sc, s_c, totC);
     unsigned long long ee = block_excl_scan<unsigned long long>(se, s_e, totE);
-    for (uint32_t g = g0; g < g1; ++g) {
+    for (uint32_t i = g0; i < g1; ++i) {
+        const uint32_t g = grp(i);
         const uint32_t c = C[g];
         S[g] = H + ec;
         E[g] = ee;
-        P[g] = make_uint2(H + ec + c - 1, FILL[g]); // each group's open block
+        P[i] = make_uint2(H + ec + c - 1, FILL[g]); // each group's open block, in logical order
         ec += c;
         ee += (unsigned long long)(c - 1) * b + FILL[g];
     }
@@ -787,14 +801,20 @@ __global__ void __launch_bounds__(FX_T) k_fixup_scan(const uint32_t *C, const ui
             set_status(ST_INTERNAL); // unallocated-block count
     }
     __syncthreads(); // S, E visible to the whole block
-    // next round's chunk bounds: first logical block whose first element is
-    // at position >= floor(q*n/p)
+    // next round's chunk bounds: EVEN, the first logical block whose first
+    // element is at position >= floor(q*n/p); SPLIT, the first block of
+    // bucket q (group (q, 0)); PER_CHUNK, the first block of chunk q (group
+    // (0, q))
     for (uint32_t qq = t; qq <= p; qq += FX_T) {
         uint32_t v;
         if (qq == 0) {
             v = H;
         } else if (qq == p) {
             v = f_new;
+        } else if (mode == FIX_SPLIT) {
+            v = S[qq * p];
+        } else if (mode == FIX_PER_CHUNK) {
+            v = S[qq];
         } else {
             const unsigned long long e = (unsigned long long)(((unsigned __int128)qq * n) / p);
             uint32_t l = 0, r = G;
@@ -875,12 +895,14 @@ __global__ void k_fixup_place(const uint32_t *pi_old, uint32_t *pi_new, const ui
 }
 
 cudaError_t launch_fixup(const Geom &g, const Bufs &w, const uint32_t *pi_old, uint32_t *pi_new,
-                         const uint32_t *UC, const uint32_t *lo_old, uint32_t *lo_new,
+                         const uint32_t *UC, const uint32_t *lo_old, uint32_t *lo_new, int mode,
                          cudaStream_t st)
 {
+    if ((mode == FIX_SPLIT && g.p != g.sigma) || mode < FIX_EVEN || mode > FIX_PER_CHUNK)
+        return cudaErrorInvalidValue;
     k_fixup_scan<<<1, FX_T, 0, st>>>(w.C, w.FILL, w.S, w.E, w.P, w.Aal, lo_old, lo_new, w.LOff,
                                      w.state, g.G, g.p, g.sigma, g.H, g.npi, g.b,
-                                     (unsigned long long)g.n);
+                                     (unsigned long long)g.n, mode);
     int blocks = static_cast<int>((g.npi + 255) / 256);
     if (blocks > 8192)
         blocks = 8192;

@@ -19,9 +19,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libradsort_gb300.so")
 RADSORT_OK, RADSORT_EINVAL, RADSORT_ENOMEM, RADSORT_ECUDA, RADSORT_ETIMEOUT, RADSORT_EINTERNAL = range(6)
 RADSORT_KEY_FLOAT32 = 0x1
 RADSORT_LAYOUT_AUTO, RADSORT_LAYOUT_CHUNKS, RADSORT_LAYOUT_GRID, RADSORT_LAYOUT_SCRATCH = 0, 1, 2, 3
+RADSORT_LAYOUT_MSD = 4
 RADSORT_SCRATCH_MAX_N = 1 << 18
 LAYOUTS = {"auto": RADSORT_LAYOUT_AUTO, "chunks": RADSORT_LAYOUT_CHUNKS, "grid": RADSORT_LAYOUT_GRID,
-           "scratch": RADSORT_LAYOUT_SCRATCH}
+           "scratch": RADSORT_LAYOUT_SCRATCH, "msd": RADSORT_LAYOUT_MSD}
 
 
 class RadsortError(RuntimeError):

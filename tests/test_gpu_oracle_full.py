@@ -4,8 +4,8 @@ oracle (bit-exact: the stable sort has one result).
   * 2^28 uint32 keys + index payload, 8-bit digits, six distributions
     (uniform, Zipf(1.1) over 2^16 values, all equal, sorted, reverse sorted,
     float32 N(0,1) through the order-preserving transform), in the automatic
-    plan (the grid layout the benchmark times) and in the chunk layout with
-    one chunk per SM;
+    plan (the grid layout the benchmark times), in the chunk layout with
+    one chunk per SM and with the MSD split (Sec. 4.3);
   * 2^30 uint32 keys + index, uniform, 8-bit digits (the benchmark's headline
     workload, automatic plan);
   * 2^30 uint64 keys uniform over 64 bits + uint32 index, 8-bit digits
@@ -72,9 +72,11 @@ def expected():
     os.rmdir(d)
 
 
-@pytest.mark.parametrize("plan", ["auto", "chunks"])
+@pytest.mark.parametrize("plan", ["auto", "chunks", "msd"])
 @pytest.mark.parametrize("dist", list(W.DISTRIBUTIONS))
 def test_2p28_u32_six_distributions_vs_oracle(dist, plan, expected):
+    """The automatic plan (grid layout), the chunk layout with one chunk per
+    SM, and the MSD split (Sec. 4.3) on the same inputs."""
     n = 1 << 28
     host = W.make_keys(dist, n)
     kt = torch.from_numpy(host.view(np.int32)).to(DEV)
@@ -83,7 +85,8 @@ def test_2p28_u32_six_distributions_vs_oracle(dist, plan, expected):
         bs, pc = 256, torch.cuda.get_device_properties(0).multi_processor_count
     else:
         bs, pc = 0, 0
-    R.sort_tensors(kt, vt, float_keys=dist == "float", block_size=bs, num_chunks=pc)
+    R.sort_tensors(kt, vt, float_keys=dist == "float", block_size=bs, num_chunks=pc,
+                   layout="msd" if plan == "msd" else 0)
     R.radsort_device_status()
     ek, ev = expected(("u32", dist, 28))
     assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)

@@ -323,3 +323,48 @@ def test_autotune_plan_sorts_and_inputs_untouched(kb, db):
     gk, gv = gpu_sort(keys, vals, digit_bits=db, block_size=b, num_chunks=p, layout=lay)
     ek, ev = oracle_sort(keys, vals, 8 * kb, db)
     assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("bs", [0, 64, 256])
+@pytest.mark.parametrize("n", [2, 63, 4097, 65543, 300001, 1 << 20])
+def test_msd_split_layout(n, bs):
+    """The MSD split (Sec. 4.3): the sorted result equals the oracle's, and
+    the sequence after every round equals the oracle's split-then-bucket
+    sequence (round 1 the top digit, then each bucket from its lowest
+    digit)."""
+    rng = np.random.default_rng(n + bs)
+    for keys in (rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32),
+                 (rng.integers(0, 40, n, dtype=np.uint64) * np.uint64(0x01010101)).astype(np.uint32)):
+        vals = W.index_payload(n)
+        gk, gv = gpu_sort(keys, vals, block_size=bs, layout="msd")
+        ek, ev = oracle_sort(keys, vals, 32, 8)
+        assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+        if n > 300001:
+            continue
+        for r in range(1, 4):
+            kt, vt = to_dev(keys), to_dev(vals)
+            ok, ov = torch.empty_like(kt), torch.empty_like(vt)
+            R.sort_rounds_tensors(kt, vt, r, ok, ov, digit_bits=8, block_size=bs, layout="msd")
+            R.radsort_device_status()
+            lk, lv = oracle.msd_split(keys, vals, n_t=4, sigma=256, bits=8, b=256, rounds=r)
+            assert np.array_equal(from_dev(ok, np.uint32), lk.astype(np.uint32)), r
+            assert np.array_equal(from_dev(ov, np.uint32), lv), r
+
+
+@pytest.mark.parametrize("with_vals", [True, False])
+def test_msd_split_u64(with_vals):
+    n = 200003
+    keys = W.make_keys("uniform", n, 64)
+    keys[::4] = keys[1]
+    vals = W.index_payload(n) if with_vals else None
+    gk, gv = gpu_sort(keys, vals, layout="msd")
+    ek, ev = oracle_sort(keys, W.index_payload(n), 64, 8)
+    assert np.array_equal(gk, ek)
+    if with_vals:
+        assert np.array_equal(gv, ev)
+
+
+def test_msd_split_rejects_11_bit_digits():
+    kt = torch.zeros(1000, dtype=torch.int32, device=DEV)
+    with pytest.raises(R.RadsortError):
+        R.sort_tensors(kt, None, digit_bits=11, layout="msd")

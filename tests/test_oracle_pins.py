@@ -378,3 +378,39 @@ def test_truncate_mutants():
         assert res[0]
         wrong += not res[1]
     assert wrong > 0
+
+
+# ---------------------------------------------------------------- MSD split (Sec. 4.3)
+@pytest.mark.parametrize("n,b", [(1, 4), (37, 1), (1000, 4), (5000, 16)])
+def test_msd_split_sequences(n, b):
+    """After the split the sequence is the stable sort by the top digit; after
+    r rounds the stable sort by (top digit, r-1 lowest digits); after n_t
+    rounds the stable sort by the whole key (numpy lexsort / argsort, both
+    stable)."""
+    rng = np.random.default_rng(n + b)
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64)
+    keys[::3] = keys[0]  # ties
+    vals = np.arange(n, dtype=np.uint32)
+    top = keys >> np.uint64(24)
+    for r in range(5):
+        k, v = oracle.msd_split(keys, vals, n_t=4, sigma=256, bits=8, b=b, rounds=r)
+        if r == 0:
+            o = np.arange(n)
+        else:
+            low = keys & np.uint64((1 << (8 * (r - 1))) - 1)
+            o = np.lexsort((low, top))
+        assert np.array_equal(v, o.astype(np.uint32)), r
+        assert np.array_equal(k, keys[o]), r
+    assert np.array_equal(v, stable_ref(keys).astype(np.uint32))
+
+
+def test_msd_split_small_alphabet_brute_force():
+    """Every array of n <= 5 two-bit keys of 3 digits (sigma = 4): the split
+    then per-bucket rounds give the unique stable sort."""
+    for n in range(1, 6):
+        for keys in itertools.product(range(8), repeat=n):
+            keys = np.array(keys, dtype=np.uint64) * np.uint64(9)  # digits vary at every position
+            vals = np.arange(n, dtype=np.uint32)
+            k, v = oracle.msd_split(keys, vals, n_t=3, sigma=4, bits=2, b=2)
+            o = np.argsort(keys, kind="stable")
+            assert np.array_equal(v, o.astype(np.uint32)) and np.array_equal(k, keys[o])
