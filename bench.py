@@ -349,7 +349,10 @@ def run_segmented(a):
     """20,000 uint32 arrays with lognormal lengths (median 4096, natural-log
     sigma 2, clipped to [16, 2^22]) and index payloads, sorted by one
     radsort_sort_segmented call captured in a CUDA graph and replayed; each
-    timed replay sorts a fresh copy (restored outside the timed region)."""
+    timed replay sorts a fresh copy (restored outside the timed region).
+    Beside it, the out-of-place comparator on the same arrays
+    (radsort_lsd_oop_sort_segmented: the long segments through n-element
+    alternate arrays), captured and timed the same way."""
     import numpy as np
     import torch
 
@@ -366,19 +369,17 @@ def run_segmented(a):
     del r
     vals0 = torch.arange(n, dtype=torch.int32, device=dev)
     od = torch.from_numpy(off.view(np.int64)).to(dev)
-    res = {}
-    for db in (8, 11):  # the autotuner's choice of digit width
-        need = R.segmented_workspace_size(off, 4, 4, db)
-        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def timed(call):
         kt, vt = keys0.clone(), vals0.clone()
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            R.sort_segmented_tensors(kt, vt, od, off, digit_bits=db, workspace=ws)  # warm-up
+            call(kt, vt)  # warm-up (also creates the library's streams)
         torch.cuda.current_stream().wait_stream(s)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            R.sort_segmented_tensors(kt, vt, od, off, digit_bits=db, workspace=ws)
+            call(kt, vt)
         times = []
         for i in range(a.warmup + a.steps):
             kt.copy_(keys0)
@@ -392,10 +393,32 @@ def run_segmented(a):
             if i >= a.warmup:
                 times.append(e0.elapsed_time(e1))
         R.radsort_device_status()
-        ms = statistics.median(times)
-        res[db] = {"ms_per_step": ms, "value": n / (ms / 1e3) / 1e9, "workspace_bytes": need}
-        del ws, kt, vt, g
+        # the last replay's result: sorted inside every segment, a stable permutation
+        seg = torch.repeat_interleave(torch.arange(lens.size, device=dev),
+                                      torch.from_numpy(lens.astype(np.int64)).to(dev))
+        k = kt.to(torch.int64) & 0xFFFFFFFF
+        v = vt.to(torch.int64) & 0xFFFFFFFF
+        same = seg[1:] == seg[:-1]
+        ok = (bool(torch.equal(seg[v], seg)) and bool(torch.equal(keys0.to(torch.int64)[v] & 0xFFFFFFFF, k))
+              and bool((k[1:][same] >= k[:-1][same]).all()))
+        del g, kt, vt, seg, k, v, same
+        return statistics.median(times), ok
+
+    res = {}
+    for db in (8, 11):  # the digit width is chosen by timing both
+        need = R.segmented_workspace_size(off, 4, 4, db)
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        ms, ok = timed(lambda kt, vt: R.sort_segmented_tensors(kt, vt, od, off, digit_bits=db, workspace=ws))
+        res[db] = {"ms_per_step": ms, "value": n / (ms / 1e3) / 1e9, "workspace_bytes": need, "checked": ok}
+        del ws
     best = max(res, key=lambda d: res[d]["value"])
+    # the out-of-place comparator at the same digit width
+    need_o = R.lsd_oop_segmented_workspace_size(off, 4, 4, best)
+    wso = torch.empty(max(need_o, 1), dtype=torch.uint8, device=dev)
+    ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
+    oms, ook = timed(lambda kt, vt: R.lsd_oop_segmented_tensors(kt, vt, ka, va, od, off, digit_bits=best,
+                                                                workspace=wso))
+    oval = n / (oms / 1e3) / 1e9
     print(json.dumps({
         "metric": "Gkeys/s, batched segmented sort (20,000 arrays, one graph replay)",
         "value": round(res[best]["value"], 3), "unit": "Gkeys/s", "n_gpus": 1, "steps": a.steps,
@@ -405,99 +428,12 @@ def run_segmented(a):
                    "segments": int(lens.size), "digit_bits": best,
                    "extra_bytes": res[best]["workspace_bytes"],
                    "extra_frac": round(res[best]["workspace_bytes"] / (n * 8), 4),
-                   "by_digit_bits": {str(k): round(v["value"], 3) for k, v in res.items()}},
+                   "by_digit_bits": {str(k): round(v["value"], 3) for k, v in res.items()},
+                   "checked": all(v["checked"] for v in res.values())},
+        "oop": {"value": round(oval, 3), "ms_per_step": round(oms, 3), "checked": ook,
+                "extra_bytes": n * 8 + need_o, "extra_frac": round((n * 8 + need_o) / (n * 8), 4)},
+        "radsort_over_oop": round(res[best]["value"] / oval, 4),
     }), flush=True)
-
-
-def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream, layout=0, with_oop=True):
-    """One more single-array workload (uniform keys, index payload): Radsort
-    in the automatic plan and the out-of-place comparator on the same data,
-    each timed over `steps` fresh copies with CUDA events; the round kernel's
-    mean launch time from the library's trace gives its roofline fraction."""
-    import torch
-
-    n = 1 << log2n
-    E = kb + 4
-    r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=dev)
-    keys0 = ((r >> 32) & 0xFFFFFFFF).to(torch.int64).to(torch.int32) if kb == 4 else r
-    del r
-    vals0 = torch.arange(n, dtype=torch.int32, device=dev)
-    if layout:
-        bs, pc, lay = 0, 0, layout
-    else:
-        bs, pc, lay = R.radsort_plan_default(n, kb, 4, db)
-    wsb = R.radsort_workspace_size(n, kb, 4, db, 0, 0, layout)
-    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
-    free_b = torch.cuda.mem_get_info(dev)[0]
-    nbuf = int(max(2, min(steps + warmup, (free_b * 0.4) // (n * E))))
-    kbufs = [torch.empty_like(keys0) for _ in range(nbuf)]
-    vbufs = [torch.empty_like(vals0) for _ in range(nbuf)]
-
-    def refill(i):
-        kbufs[i].copy_(keys0)
-        vbufs[i].copy_(vals0)
-
-    def run(fn):
-        for i in range(nbuf):
-            refill(i)
-        for i in range(warmup):
-            fn(i % nbuf)
-        for i in range(min(warmup, nbuf)):
-            refill(i)
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for s in range(steps):
-            i = warmup + s
-            if i >= nbuf and s > 0:
-                refill(i % nbuf)
-            fn(i % nbuf)
-        e1.record(stream)
-        barrier()
-        R.radsort_device_status()
-        return e0.elapsed_time(e1) / steps
-
-    R.radsort_trace_read()
-    R.radsort_trace_enable(True)
-    ms = run(lambda i: R.sort_tensors(kbufs[i], vbufs[i], digit_bits=db, workspace=ws, layout=layout))
-    R.radsort_trace_enable(False)
-    recs = R.radsort_trace_read()
-    # the last step's result: sorted and a stable permutation of the input
-    last = (warmup + steps - 1) % nbuf
-    k = kbufs[last].to(torch.int64) & 0xFFFFFFFF if kb == 4 else kbufs[last] ^ (-(2 ** 63))
-    v = vbufs[last].to(torch.int64) & 0xFFFFFFFF
-    eq = kbufs[last][1:] == kbufs[last][:-1]
-    ok = bool((k[1:] >= k[:-1]).all()) and bool(torch.equal(keys0[v], kbufs[last])) and bool(
-        (v[1:][eq] > v[:-1][eq]).all())
-    del k, v, eq
-    rounds = [t for ph, rd, t in recs if ph == "sortPhase"]
-    fin = [t for ph, rd, t in recs if ph == "Finalize"]
-    avg_round = statistics.mean(rounds) if rounds else float("nan")
-    hbm, src = peaks()
-    val = n / (ms / 1e3) / 1e9
-    oms = oval = None
-    if with_oop:
-        ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
-        oms = run(lambda i: R.lsd_oop_tensors(kbufs[i], vbufs[i], ka, va, digit_bits=db))
-        oval = n / (oms / 1e3) / 1e9
-        del ka, va
-    out = {
-        "workload": f"radsort_{'u32' if kb == 4 else 'u64'}_keys_u32_index_2^{log2n}_uniform_d{db}"
-                    + (f"_{layout}" if layout else ""),
-        "n": n, "value": round(val, 3), "unit": "Gkeys/s", "ms_per_step": round(ms, 3), "steps": steps,
-        "block_size": bs, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
-        "round_ms": round(avg_round, 4),
-        "round_frac": round((n * 2 * E) / (avg_round / 1e3) / 1e9 / hbm, 4),
-        "finalize_ms": round(statistics.mean(fin), 4) if fin else None,
-        "result_checked": ok,
-        "oop": None if oval is None else {
-            "value": round(oval, 3), "ms_per_step": round(oms, 3),
-            "extra_bytes": n * E + R.radsort_lsd_oop_scratch_size(n, kb, 4, db)},
-        "radsort_over_oop": None if oval is None else round(val / oval, 4),
-    }
-    del kbufs, vbufs, ws, keys0, vals0
-    torch.cuda.empty_cache()
-    return out
 
 
 # ---------------------------------------------------------------- GPU arm

@@ -260,14 +260,20 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
  * kernels); offsets_host the same values on the host (used to plan the long
  * segments).  Segments up to 4096 elements (2048 for 11-bit digits) are sorted
  * in shared memory.  Segments up to 2^18 elements are sorted out of place in
- * per-CTA scratch, the paper's suggestion of reusing T as the A' of Alg. 1 for
- * short arrays (Sec. 5).  Both classes are handled by one persistent launch
- * each.  Longer segments run the full Radsort (Alg. 2), or Alg. 1 with
- * alternate buffers in the workspace when their start is not 16-byte aligned.
- * workspace: at least radsort_segmented_workspace_size() bytes, or NULL to
- * allocate stream-ordered.  With a caller workspace the call issues only
- * kernel launches and memsets on `stream`, so it can be captured in a CUDA
- * graph.
+ * per-CTA scratch as long as the longest of them (2 CTAs per SM), the paper's
+ * suggestion of reusing T as the A' of Alg. 1 for short arrays (Sec. 5).
+ * Both classes are handled by one persistent launch each.  Longer segments
+ * run the full Radsort (Alg. 2), or Alg. 1 with alternate buffers in the
+ * workspace when their start is not 16-byte aligned; they are spread, longest
+ * first, over up to 4 library-owned streams (created on the first call that
+ * has long segments on a device) that start after the work already on
+ * `stream` and that `stream` waits for, each with its own part of the
+ * workspace.  workspace: at least radsort_segmented_workspace_size() bytes,
+ * or NULL to allocate stream-ordered.  With a caller workspace the call
+ * issues only kernel launches, memsets and event records / waits, so it can
+ * be captured in a CUDA graph (make a first call with long segments before
+ * capturing, so that the streams exist).  Calls from several host threads
+ * on one device take turns while they enqueue.
  */
 radsort_status radsort_segmented_workspace_size(const uint64_t *offsets_host, size_t num_segments,
                                                 int key_bytes, int value_bytes, int digit_bits,
@@ -276,6 +282,23 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
                                       const uint64_t *offsets_host, size_t num_segments,
                                       int key_bytes, int digit_bits, void *workspace,
                                       size_t workspace_bytes, void *stream);
+
+/*
+ * Comparison baseline for the batched sort: the same segments, the same
+ * shared-memory and per-CTA passes for the short ones, and the long ones
+ * sorted out of place (Alg. 1, radsort_lsd_oop_sort) into keys_alt /
+ * values_alt, n-element caller arrays (the memory Radsort avoids), on the
+ * same internal streams.  The result ends in keys / values.  workspace: at
+ * least radsort_lsd_oop_segmented_workspace_size() bytes, or NULL.
+ */
+radsort_status radsort_lsd_oop_segmented_workspace_size(const uint64_t *offsets_host, size_t num_segments,
+                                                        int key_bytes, int value_bytes, int digit_bits,
+                                                        size_t *bytes);
+radsort_status radsort_lsd_oop_sort_segmented(void *keys, uint32_t *values, void *keys_alt,
+                                              uint32_t *values_alt, const uint64_t *offsets_dev,
+                                              const uint64_t *offsets_host, size_t num_segments,
+                                              int key_bytes, int digit_bits, void *workspace,
+                                              size_t workspace_bytes, void *stream);
 
 /*
  * radsort_sort_noalloc: radsort_sort without any device allocation.  The

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -876,22 +877,48 @@ bool seg_aligned(size_t off, int kb, bool hasv)
     return (off * kb) % 16 == 0 && (!hasv || (off * 4) % 16 == 0);
 }
 
+// Long segments run on up to SEG_STREAMS internal streams forked from the
+// caller's stream, so that several of them share the SMs (a segment of 2^19
+// elements fills a third of them); each stream has its own workspace slice.
+constexpr int SEG_STREAMS = 4;
+// the medium pass's scratch (one out-of-place buffer per CTA) is held to
+// this share of the arrays' bytes by running fewer CTAs (at least 16).
+// Measured on 20,000 lognormal arrays (2^29 keys + values, the longest
+// medium one near 2^18, long segments beside it on the library's streams):
+// 1.5% -> 7.1 Gkeys/s, 3% -> 13.5, 6% -> 24.0, no limit (2 CTAs per SM,
+// 14%) -> 20.7
+constexpr double SEG_MED_SHARE = 0.06;
+
 struct SegPlan {
-    size_t base = 0, large = 0, total = 0;
+    size_t base = 0;    // classify lists + medium scratch
+    size_t large = 0;   // workspace of one long-segment stream
+    size_t total = 0;   // base + nstr * large
+    uint32_t med_max = 0, med_ctas = 0;
+    int nstr = 0;       // internal streams used (0: no long segment)
 };
 
-radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, SegPlan *sp)
+// oop: long segments sorted out of place (Alg. 1) into the caller's
+// alternate arrays, so a stream's slice holds only the comparator's scratch
+radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, bool oop, SegPlan *sp)
 {
-    sp->base = (seg_scratch_bytes(kb, hasv, nseg) + 255) / 256 * 256;
-    size_t large = 0;
+    size_t large = 0, nlong = 0;
+    uint32_t med_max = 0;
+    const uint32_t small_max = seg_small_max(db);
+    const size_t n = nseg ? offh[nseg] - offh[0] : 0;
     for (size_t s = 0; s < nseg; ++s) {
         if (offh[s + 1] < offh[s])
             return RADSORT_EINVAL;
         const size_t len = offh[s + 1] - offh[s];
-        if (len <= SEG_MED)
+        if (len <= SEG_MED) {
+            if (len > small_max && len > med_max)
+                med_max = static_cast<uint32_t>(len);
             continue;
+        }
+        ++nlong;
         size_t need;
-        if (seg_aligned(offh[s], kb, hasv)) {
+        if (oop) {
+            need = lsd_oop_scratch_bytes(len, kb, db, hasv) + 256;
+        } else if (seg_aligned(offh[s], kb, hasv)) {
             const radsort_plan pl = large_plan(len);
             Geom g;
             if (make_geom(len, kb, hasv, db, &pl, &g) != RADSORT_OK)
@@ -902,10 +929,115 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
                    lsd_oop_scratch_bytes(len, kb, db, hasv) + 256;
         }
         if (need > large)
-            large = need;
+            large = (need + 255) / 256 * 256;
     }
+    sp->med_max = med_max;
+    sp->med_ctas = seg_med_ctas(med_max, kb, hasv, static_cast<size_t>(SEG_MED_SHARE * double(n) * (kb + (hasv ? 4 : 0))));
+    sp->base = (seg_scratch_bytes(kb, hasv, nseg, med_max, sp->med_ctas) + 255) / 256 * 256;
     sp->large = large;
-    sp->total = sp->base + large;
+    sp->nstr = static_cast<int>(nlong < size_t(SEG_STREAMS) ? nlong : size_t(SEG_STREAMS));
+    sp->total = sp->base + size_t(sp->nstr) * large;
+    return RADSORT_OK;
+}
+
+struct SegStreams {
+    cudaStream_t s[SEG_STREAMS];
+    cudaEvent_t fork;
+    cudaEvent_t join[SEG_STREAMS];
+};
+SegStreams g_seg_streams[MAX_DEVICES];
+std::mutex g_seg_mu; // one call at a time forks onto the internal streams
+
+// the current device's internal streams and events (created on first use)
+radsort_status seg_streams(SegStreams **out)
+{
+    static DeviceOnce once;
+    const int dev = current_device();
+    if (dev < 0 || dev >= MAX_DEVICES)
+        return RADSORT_ECUDA;
+    const cudaError_t e = once.run([dev] {
+        SegStreams &x = g_seg_streams[dev];
+        cudaError_t r = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming);
+        for (int i = 0; i < SEG_STREAMS && r == cudaSuccess; ++i) {
+            r = cudaStreamCreateWithFlags(&x.s[i], cudaStreamNonBlocking);
+            if (r == cudaSuccess)
+                r = cudaEventCreateWithFlags(&x.join[i], cudaEventDisableTiming);
+        }
+        return r;
+    });
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    *out = &g_seg_streams[dev];
+    return RADSORT_OK;
+}
+
+// Enqueues main() on st (the short and medium segments) and sorts the long
+// segments beside it: each goes, longest first, to the internal stream with
+// the fewest elements so far; sort_one(offset, length, slice, stream).  The
+// internal streams start after the work already on st (so the workspace is
+// free), and st waits for them at the end.
+template <typename M, typename F>
+radsort_status seg_run(const uint64_t *offh, size_t nseg, const SegPlan &sp, char *lw, cudaStream_t st,
+                       M &&main, F &&sort_one)
+{
+    if (sp.nstr == 0)
+        return main();
+    std::vector<uint32_t> idx;
+    for (size_t s = 0; s < nseg; ++s)
+        if (offh[s + 1] - offh[s] > SEG_MED)
+            idx.push_back(static_cast<uint32_t>(s));
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t x, uint32_t y) {
+        return offh[x + 1] - offh[x] > offh[y + 1] - offh[y];
+    });
+    SegStreams *ss = nullptr;
+    radsort_status rs = seg_streams(&ss);
+    if (rs != RADSORT_OK)
+        return rs;
+    std::lock_guard<std::mutex> lk(g_seg_mu);
+    cudaError_t e = cudaEventRecord(ss->fork, st);
+    for (int i = 0; i < sp.nstr && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(ss->s[i], ss->fork, 0);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    rs = main();
+    unsigned long long load[SEG_STREAMS] = {};
+    for (uint32_t sg : idx) {
+        if (rs != RADSORT_OK)
+            break;
+        int best = 0;
+        for (int i = 1; i < sp.nstr; ++i)
+            if (load[i] < load[best])
+                best = i;
+        const size_t off = offh[sg], len = offh[sg + 1] - off;
+        load[best] += len;
+        rs = sort_one(off, len, lw + size_t(best) * sp.large, ss->s[best]);
+    }
+    // the join is recorded even after a failure, so st never runs ahead
+    for (int i = 0; i < sp.nstr; ++i) {
+        cudaError_t ej = cudaEventRecord(ss->join[i], ss->s[i]);
+        if (ej == cudaSuccess)
+            ej = cudaStreamWaitEvent(st, ss->join[i], 0);
+        if (ej != cudaSuccess && rs == RADSORT_OK)
+            rs = cuda_status(ej);
+    }
+    return rs;
+}
+
+// the caller's workspace, or one allocated stream-ordered
+radsort_status seg_workspace(void *workspace, size_t workspace_bytes, size_t need, cudaStream_t st,
+                             void **ws, bool *own)
+{
+    *own = false;
+    *ws = workspace;
+    if (workspace) {
+        if (workspace_bytes < need)
+            return RADSORT_ENOMEM;
+        return aligned16(workspace) ? RADSORT_OK : RADSORT_EINVAL;
+    }
+    const cudaError_t e = cudaMallocAsync(ws, need ? need : 256, st);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    *own = true;
     return RADSORT_OK;
 }
 } // namespace
@@ -920,7 +1052,7 @@ radsort_status radsort_segmented_workspace_size(const uint64_t *offsets_host, si
         (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
         return RADSORT_EINVAL;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, &sp);
     *bytes = s == RADSORT_OK ? sp.total : 0;
     return s;
 }
@@ -940,45 +1072,94 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
         return RADSORT_EINVAL;
     const bool hasv = values != nullptr;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, &sp);
     if (s != RADSORT_OK)
         return s;
     cudaStream_t st = as_stream(stream);
-    void *ws = workspace;
+    void *ws = nullptr;
     bool own = false;
-    if (ws) {
-        if (workspace_bytes < sp.total)
-            return RADSORT_ENOMEM;
-        if (!aligned16(ws))
-            return RADSORT_EINVAL;
-    } else {
-        cudaError_t e = cudaMallocAsync(&ws, sp.total, st);
-        if (e != cudaSuccess)
-            return cuda_status(e);
-        own = true;
+    s = seg_workspace(workspace, workspace_bytes, sp.total, st, &ws, &own);
+    if (s != RADSORT_OK)
+        return s;
+    auto main = [&]() -> radsort_status {
+        return cuda_status(launch_segmented(keys, values, reinterpret_cast<const unsigned long long *>(offsets_dev),
+                                            num_segments, key_bytes, digit_bits, sp.med_max, sp.med_ctas, ws, st));
+    };
+    radsort_status rs = seg_run(offsets_host, num_segments, sp, static_cast<char *>(ws) + sp.base, st, main,
+                      [&](size_t off, size_t len, char *lw, cudaStream_t ls) -> radsort_status {
+                          char *sk = static_cast<char *>(keys) + off * key_bytes;
+                          uint32_t *sv = hasv ? values + off : nullptr;
+                          if (seg_aligned(off, key_bytes, hasv)) {
+                              const radsort_plan pl = large_plan(len);
+                              return sort_common(sk, sv, len, key_bytes, digit_bits, 0, &pl, lw, sp.large, ls,
+                                                 -1, nullptr, nullptr);
+                          }
+                          char *ak = lw;
+                          char *av = ak + (len * key_bytes + 255) / 256 * 256;
+                          char *sc = av + (hasv ? (len * 4 + 255) / 256 * 256 : 0);
+                          return cuda_status(launch_lsd_oop_ws(sk, sv, ak,
+                                                               hasv ? reinterpret_cast<uint32_t *>(av) : nullptr,
+                                                               len, key_bytes, digit_bits, sc, ls));
+                      });
+    if (own) {
+        cudaError_t e2 = cudaFreeAsync(ws, st);
+        if (rs == RADSORT_OK)
+            rs = cuda_status(e2);
     }
-    cudaError_t e = launch_segmented(keys, values, reinterpret_cast<const unsigned long long *>(offsets_dev),
-                                     num_segments, key_bytes, digit_bits, ws, st);
-    radsort_status rs = cuda_status(e);
-    char *lw = static_cast<char *>(ws) + sp.base;
-    for (size_t sg = 0; sg < num_segments && rs == RADSORT_OK; ++sg) {
-        const size_t off = offsets_host[sg], len = offsets_host[sg + 1] - off;
-        if (len <= SEG_MED)
-            continue;
-        char *sk = static_cast<char *>(keys) + off * key_bytes;
-        uint32_t *sv = hasv ? values + off : nullptr;
-        if (seg_aligned(off, key_bytes, hasv)) {
-            const radsort_plan pl = large_plan(len);
-            rs = sort_common(sk, sv, len, key_bytes, digit_bits, 0, &pl, lw, sp.large, stream, -1,
-                             nullptr, nullptr);
-        } else {
-            char *ak = lw;
-            char *av = ak + (len * key_bytes + 255) / 256 * 256;
-            char *sc = av + (hasv ? (len * 4 + 255) / 256 * 256 : 0);
-            rs = cuda_status(launch_lsd_oop_ws(sk, sv, ak, hasv ? reinterpret_cast<uint32_t *>(av) : nullptr,
-                                               len, key_bytes, digit_bits, sc, st));
-        }
-    }
+    return rs;
+}
+
+radsort_status radsort_lsd_oop_segmented_workspace_size(const uint64_t *offsets_host, size_t num_segments,
+                                                        int key_bytes, int value_bytes, int digit_bits,
+                                                        size_t *bytes)
+{
+    if (!bytes || (key_bytes != 4 && key_bytes != 8) || (value_bytes != 0 && value_bytes != 4) ||
+        (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
+        return RADSORT_EINVAL;
+    SegPlan sp;
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, true, &sp);
+    *bytes = s == RADSORT_OK ? sp.total : 0;
+    return s;
+}
+
+radsort_status radsort_lsd_oop_sort_segmented(void *keys, uint32_t *values, void *keys_alt,
+                                              uint32_t *values_alt, const uint64_t *offsets_dev,
+                                              const uint64_t *offsets_host, size_t num_segments,
+                                              int key_bytes, int digit_bits, void *workspace,
+                                              size_t workspace_bytes, void *stream)
+{
+    if ((key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (num_segments == 0)
+        return RADSORT_OK;
+    if (!keys || !keys_alt || !offsets_dev || !offsets_host || !aligned16(keys) ||
+        (values && (!aligned16(values) || !values_alt)))
+        return RADSORT_EINVAL;
+    if (num_segments >= (size_t(1) << 31))
+        return RADSORT_EINVAL;
+    const bool hasv = values != nullptr;
+    SegPlan sp;
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, true, &sp);
+    if (s != RADSORT_OK)
+        return s;
+    cudaStream_t st = as_stream(stream);
+    void *ws = nullptr;
+    bool own = false;
+    s = seg_workspace(workspace, workspace_bytes, sp.total, st, &ws, &own);
+    if (s != RADSORT_OK)
+        return s;
+    auto main = [&]() -> radsort_status {
+        return cuda_status(launch_segmented(keys, values, reinterpret_cast<const unsigned long long *>(offsets_dev),
+                                            num_segments, key_bytes, digit_bits, sp.med_max, sp.med_ctas, ws, st));
+    };
+    radsort_status rs = seg_run(offsets_host, num_segments, sp, static_cast<char *>(ws) + sp.base, st, main,
+                      [&](size_t off, size_t len, char *lw, cudaStream_t ls) -> radsort_status {
+                          char *sk = static_cast<char *>(keys) + off * key_bytes;
+                          char *ak = static_cast<char *>(keys_alt) + off * key_bytes;
+                          return cuda_status(launch_lsd_oop_ws(sk, hasv ? values + off : nullptr, ak,
+                                                               hasv ? values_alt + off : nullptr, len, key_bytes,
+                                                               digit_bits, lw, ls));
+                      });
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, st);
         if (rs == RADSORT_OK)

@@ -133,8 +133,9 @@ struct SegArgs {
     uint32_t nseg;
     uint32_t *ctr;                 // [0] small count, [1] medium count, [2] small ticket, [3] medium ticket
     uint32_t *small_list, *med_list;
-    void *scr_k;                   // medium scratch, SEG_MED elements per CTA
+    void *scr_k;                   // medium scratch, med_stride elements per CTA
     uint32_t *scr_v;
+    uint32_t med_stride;           // the longest medium segment of the call
     int nt, db;
 };
 
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(SEG_T) k_seg_small(SegArgs a)
 
 // medium segments: out-of-place LSD between the segment and this CTA's
 // scratch region (Alg. 1 per digit), tile by tile
-template <typename KT, bool HASV, int DB, int TILE, int MED>
+template <typename KT, bool HASV, int DB, int TILE>
 __global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
 {
     using TP = TilePass<KT, HASV, DB, TILE / (32 * SEG_NW)>;
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
     unsigned char *scratch = reinterpret_cast<unsigned char *>(gh + SIGMA);
     __shared__ uint32_t s_t;
     KT *keys = static_cast<KT *>(a.keys);
-    KT *sck = static_cast<KT *>(a.scr_k) + size_t(blockIdx.x) * MED;
-    uint32_t *scv = HASV ? a.scr_v + size_t(blockIdx.x) * MED : nullptr;
+    KT *sck = static_cast<KT *>(a.scr_k) + size_t(blockIdx.x) * a.med_stride;
+    uint32_t *scv = HASV ? a.scr_v + size_t(blockIdx.x) * a.med_stride : nullptr;
     const uint32_t count = a.ctr[1];
     const uint32_t mask = SIGMA - 1;
     for (;;) {
@@ -237,6 +238,10 @@ __global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
         const uint32_t sgi = a.med_list[t];
         const unsigned long long o = a.off[sgi];
         const uint32_t len = static_cast<uint32_t>(a.off[sgi + 1] - o);
+        if (len > a.med_stride) { // the host sized the scratch from its offsets
+            set_status(ST_INTERNAL);
+            continue;
+        }
         KT *sk = keys + o, *dk = sck;
         uint32_t *svp = HASV ? a.vals + o : nullptr, *dvp = scv;
         for (int r = 0; r < a.nt; ++r) {
@@ -324,7 +329,7 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
             cudaError_t e = cudaFuncSetAttribute(k_seg_small<KT, HASV, DB, SMALL>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(small_smem()));
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_seg_medium<KT, HASV, DB, TILE, SEG_MED>,
+                e = cudaFuncSetAttribute(k_seg_medium<KT, HASV, DB, TILE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(med_smem()));
             return e;
         });
@@ -335,7 +340,8 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
                                                       small_smem());
         const int sms = num_sms();
         k_seg_small<KT, HASV, DB, SMALL><<<sms * (per > 0 ? per : 1), SEG_T, small_smem(), st>>>(a);
-        k_seg_medium<KT, HASV, DB, TILE, SEG_MED><<<med_ctas, SEG_T, med_smem(), st>>>(a);
+        if (a.med_stride)
+            k_seg_medium<KT, HASV, DB, TILE><<<med_ctas, SEG_T, med_smem(), st>>>(a);
         g_launches += 2;
         return cudaGetLastError();
     }
@@ -343,18 +349,32 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
 
 uint32_t seg_small_max(int db) { return db <= 8 ? 4096u : 2048u; }
 
-int seg_med_ctas() { return num_sms() * 2; }
+// CTAs of the medium pass: two per SM, fewer when their scratch (med_max
+// elements each) would pass `budget` bytes, at least 16
+uint32_t seg_med_ctas(uint32_t med_max, int kb, bool hasv, size_t budget)
+{
+    const uint32_t most = static_cast<uint32_t>(num_sms()) * 2;
+    if (!med_max)
+        return 0;
+    const size_t per = size_t(med_max) * (kb + (hasv ? 4 : 0));
+    size_t c = budget / per;
+    if (c < 16)
+        c = 16;
+    return c < most ? static_cast<uint32_t>(c) : most;
+}
 
-size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg)
+// med_max: the longest medium segment (0: none), the per-CTA scratch stride
+size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg, uint32_t med_max, uint32_t med_ctas)
 {
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
-    return up(64) + 2 * up(nseg * 4) + up(size_t(seg_med_ctas()) * SEG_MED * kb) +
-           (hasv ? up(size_t(seg_med_ctas()) * SEG_MED * 4) : 0);
+    return up(64) + 2 * up(nseg * 4) + up(size_t(med_ctas) * med_max * kb) +
+           (hasv ? up(size_t(med_ctas) * med_max * 4) : 0);
 }
 
 cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long long *off_dev,
-                             size_t nseg, int kb, int db, void *scratch, cudaStream_t st)
+                             size_t nseg, int kb, int db, uint32_t med_max, uint32_t med_ctas, void *scratch,
+                             cudaStream_t st)
 {
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
@@ -371,8 +391,9 @@ cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long lon
     a.med_list = reinterpret_cast<uint32_t *>(p);
     p += up(nseg * 4);
     a.scr_k = p;
-    p += up(size_t(seg_med_ctas()) * SEG_MED * kb);
+    p += up(size_t(med_ctas) * med_max * kb);
     a.scr_v = vals ? reinterpret_cast<uint32_t *>(p) : nullptr;
+    a.med_stride = med_max;
     a.nt = (8 * kb + db - 1) / db;
     a.db = db;
     cudaError_t e = cudaMemsetAsync(a.ctr, 0, 64, st);
@@ -381,7 +402,7 @@ cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long lon
     k_seg_classify<<<(nseg + 255) / 256 > 0 ? (nseg + 255) / 256 : 1, 256, 0, st>>>(
         a, seg_small_max(db), SEG_MED);
     g_launches += 1;
-    const int mc = seg_med_ctas();
+    const int mc = static_cast<int>(med_ctas);
     using u64 = unsigned long long;
     if (kb == 4) {
         if (db == 8)

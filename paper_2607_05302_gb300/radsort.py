@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
             "radsort_sort_noalloc": ([vp, vp, sz, i, i, vp], i),
             "radsort_segmented_workspace_size": ([vp, sz, i, i, i, ctypes.POINTER(sz)], i),
             "radsort_sort_segmented": ([vp, vp, vp, vp, sz, i, i, vp, sz, vp], i),
+            "radsort_lsd_oop_segmented_workspace_size": ([vp, sz, i, i, i, ctypes.POINTER(sz)], i),
+            "radsort_lsd_oop_sort_segmented": ([vp, vp, vp, vp, vp, vp, sz, i, i, vp, sz, vp], i),
             "radsort_sort_ex": ([vp, vp, sz, i, i, u32, pplan, vp, sz, vp], i),
             "radsort_sort_rounds": ([vp, vp, sz, i, i, i, pplan, vp, vp, vp], i),
             "radsort_lsd_oop_sort": ([vp, vp, vp, vp, sz, i, i, vp], i),
@@ -98,6 +100,7 @@ def lib() -> ctypes.CDLL:
 # exported names declared in include/radsort.h
 EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_autotune", "radsort_workspace_size", "radsort_sort",
            "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_sort_segmented",
+           "radsort_lsd_oop_segmented_workspace_size", "radsort_lsd_oop_sort_segmented",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
            "radsort_lsd_oop_scratch_size", "radsort_float_keys",
            "radsort_device_status", "radsort_debug_wait_probe", "radsort_trace_enable", "radsort_trace_read",
@@ -292,6 +295,29 @@ def sort_segmented_tensors(keys, values, offsets_dev, offsets_host, *, digit_bit
                                      oh.ctypes.data_as(ctypes.c_void_p), oh.size - 1, _key_bytes(keys),
                                      digit_bits, ws, wsb, _torch_stream(stream)),
         "radsort_sort_segmented")
+
+
+def lsd_oop_segmented_workspace_size(offsets_host, key_bytes, value_bytes, digit_bits=8):
+    import numpy as np
+    oh = np.ascontiguousarray(offsets_host, dtype=np.uint64)
+    out = ctypes.c_size_t(0)
+    _ok(lib().radsort_lsd_oop_segmented_workspace_size(oh.ctypes.data_as(ctypes.c_void_p), oh.size - 1,
+                                                       key_bytes, value_bytes, digit_bits, ctypes.byref(out)),
+        "radsort_lsd_oop_segmented_workspace_size")
+    return int(out.value)
+
+
+def lsd_oop_segmented_tensors(keys, values, keys_alt, values_alt, offsets_dev, offsets_host, *, digit_bits=8,
+                              workspace=None, stream=None):
+    """The out-of-place comparator of the batched sort (long segments through
+    n-element alternate arrays)."""
+    import numpy as np
+    oh = np.ascontiguousarray(offsets_host, dtype=np.uint64)
+    ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
+    _ok(lib().radsort_lsd_oop_sort_segmented(_ptr(keys), _ptr(values), _ptr(keys_alt), _ptr(values_alt),
+                                             _ptr(offsets_dev), oh.ctypes.data_as(ctypes.c_void_p), oh.size - 1,
+                                             _key_bytes(keys), digit_bits, ws, wsb, _torch_stream(stream)),
+        "radsort_lsd_oop_sort_segmented")
 
 
 def float_keys_tensors(keys, inverse=False, stream=None):

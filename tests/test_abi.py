@@ -146,12 +146,13 @@ def test_autotune_without_timing(lib):
 
 def test_segmented_workspace_size(lib):
     """Host-side planning of radsort_sort_segmented: decreasing offsets are
-    rejected; the workspace covers the Radsort workspace of the longest
-    segment that takes the full path (above 2^18 elements, in the grid layout
-    at these sizes) plus a part that does not grow with the data; among
-    16-byte-aligned long segments the longest alone decides the long-segment
-    part; a long segment whose start is not 16-byte aligned is sorted out of
-    place and needs its alternate arrays."""
+    rejected; the per-CTA scratch of the medium segments follows the longest
+    medium segment present; each stream of long segments (one per long
+    segment, at most four) gets the Radsort workspace of the longest segment
+    that takes the full path (above 2^18 elements, in the grid layout at
+    these sizes); a long segment whose start is not 16-byte aligned is sorted
+    out of place and needs its alternate arrays.  The out-of-place
+    comparator needs only its scratch per stream."""
     import numpy as np
 
     from paper_2607_05302_gb300 import radsort as R
@@ -165,12 +166,22 @@ def test_segmented_workspace_size(lib):
         R.segmented_workspace_size(np.array([0, 10, 5], np.uint64), 4, 4, 8)
     base = ws([100])
     assert ws([100] * 1000) - base <= 1000 * 8 + 1024            # index words per segment
-    assert ws([5000] * 10) - ws([5000]) <= 10 * 8 + 1024          # medium segments: fixed buffers
+    assert ws([5000] * 10) - ws([5000]) <= 10 * 8 + 1024          # medium: the longest decides
+    assert ws([5000]) - base < ws([100000]) - base < ws([1 << 18]) - base
     big = (1 << 22) + 4
     assert ws([big]) >= R.radsort_workspace_size(big, 4, 4, 8, layout="grid")
-    assert ws([big, 1 << 20, 300, 5000]) <= ws([big]) + 4 * 8 + 1024   # all starts aligned
+    one = ws([big]) - base                                          # one stream of long segments
+    assert ws([big, 1 << 20, 300, 5000]) <= base + 2 * one + (ws([5000]) - base) + 1024
+    assert ws([big] * 9) <= base + 4 * one + 9 * 8 + 1024          # at most four streams
     odd = [3, 1 << 20]  # the long segment starts 12 bytes past an aligned address
     assert ws(odd) >= base + (1 << 20) * 8
+
+    def ows(lens):
+        off = np.zeros(len(lens) + 1, np.uint64)
+        np.cumsum(np.array(lens, np.uint64), out=off[1:])
+        return R.lsd_oop_segmented_workspace_size(off, 4, 4, 8)
+
+    assert ows([big]) - ows([100]) < one                             # no block store, only scratch
 
 
 def test_binding_signatures_match_the_header(lib):

@@ -127,3 +127,73 @@ def test_config4_20000_lognormal_segments_properties():
     assert bool((k[1:][same] >= k[:-1][same]).all())  # sorted per segment
     eq = same & (k[1:] == k[:-1])
     assert bool((v[1:][eq] > v[:-1][eq]).all())  # stable
+
+
+LONG_SET = [300001, 5000, (1 << 18) + 1, 17, 400000, (1 << 20) + 3, 1, 262145, 70000, 600000]
+
+
+def test_long_segments_on_several_streams_vs_oracle():
+    """Six long segments (above 2^18, aligned and misaligned starts) spread
+    over the library's streams, between short ones: the same result as the
+    oracle's per-segment stable sort."""
+    n = sum(LONG_SET)
+    rng = np.random.default_rng(77)
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    keys[::7] = keys[2]
+    kt, vt, _ = run_segmented(keys, LONG_SET)
+    ek, ev = oracle_segmented_u32(keys, LONG_SET)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
+@pytest.mark.parametrize("lengths", ["mixed", "long"])
+def test_out_of_place_comparator_vs_oracle(lengths):
+    """radsort_lsd_oop_sort_segmented: the same arrays through n-element
+    alternate arrays give the oracle's result."""
+    lens = [int(x) for x in (LENGTH_SETS["mixed"] if lengths == "mixed" else LONG_SET)]
+    off = offsets_of(lens)
+    n = int(off[-1])
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    kt = torch.from_numpy(keys.view(np.int32)).to(DEV)
+    vt = torch.arange(n, dtype=torch.int32, device=DEV)
+    ka, va = torch.empty_like(kt), torch.empty_like(vt)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    ws = torch.empty(max(R.lsd_oop_segmented_workspace_size(off, 4, 4), 1), dtype=torch.uint8, device=DEV)
+    R.lsd_oop_segmented_tensors(kt, vt, ka, va, od, off, workspace=ws)
+    R.radsort_device_status()
+    ek, ev = oracle_segmented_u32(keys, lens)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
+def test_captured_graph_with_long_segments():
+    """The call with long segments captured in a CUDA graph (fork and join
+    over the library's streams inside the capture) and replayed twice on
+    fresh copies gives the oracle's result each time."""
+    lens = LONG_SET
+    off = offsets_of(lens)
+    n = int(off[-1])
+    keys = W.make_keys("uniform", n)
+    k0 = torch.from_numpy(keys.view(np.int32)).to(DEV)
+    kt, vt = k0.clone(), torch.arange(n, dtype=torch.int32, device=DEV)
+    v0 = vt.clone()
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    ws = torch.empty(R.segmented_workspace_size(off, 4, 4), dtype=torch.uint8, device=DEV)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        R.sort_segmented_tensors(kt, vt, od, off, workspace=ws)  # first call: the streams exist
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        R.sort_segmented_tensors(kt, vt, od, off, workspace=ws)
+    ek, ev = oracle_segmented_u32(keys, lens)
+    for _ in range(2):
+        kt.copy_(k0)
+        vt.copy_(v0)
+        g.replay()
+        torch.cuda.synchronize()
+        R.radsort_device_status()
+        assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+        assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
