@@ -405,13 +405,14 @@ def run_segmented(a):
         return statistics.median(times), ok
 
     res = {}
-    for db in (8, 11):  # the digit width is chosen by timing both
+    for db in (8, 11):  # both widths, for the record
         need = R.segmented_workspace_size(off, 4, 4, db)
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
         ms, ok = timed(lambda kt, vt: R.sort_segmented_tensors(kt, vt, od, off, digit_bits=db, workspace=ws))
         res[db] = {"ms_per_step": ms, "value": n / (ms / 1e3) / 1e9, "workspace_bytes": need, "checked": ok}
         del ws
-    best = max(res, key=lambda d: res[d]["value"])
+    # the digit width the library's autotuner picks for this batch
+    best = R.segmented_autotune(keys0, vals0, od, off)
     # the out-of-place comparator at the same digit width
     need_o = R.lsd_oop_segmented_workspace_size(off, 4, 4, best)
     wso = torch.empty(max(need_o, 1), dtype=torch.uint8, device=dev)
@@ -429,11 +430,103 @@ def run_segmented(a):
                    "extra_bytes": res[best]["workspace_bytes"],
                    "extra_frac": round(res[best]["workspace_bytes"] / (n * 8), 4),
                    "by_digit_bits": {str(k): round(v["value"], 3) for k, v in res.items()},
+                   "digit_bits_from": "radsort_segmented_autotune",
                    "checked": all(v["checked"] for v in res.values())},
         "oop": {"value": round(oval, 3), "ms_per_step": round(oms, 3), "checked": ook,
                 "extra_bytes": n * 8 + need_o, "extra_frac": round((n * 8 + need_o) / (n * 8), 4)},
         "radsort_over_oop": round(res[best]["value"] / oval, 4),
     }), flush=True)
+
+
+def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream, layout=0, with_oop=True):
+    """One more single-array workload (uniform keys, index payload): Radsort
+    in the automatic plan and the out-of-place comparator on the same data,
+    each timed over `steps` fresh copies with CUDA events; the round kernel's
+    mean launch time from the library's trace gives its roofline fraction."""
+    import torch
+
+    n = 1 << log2n
+    E = kb + 4
+    r = W.splitmix64_torch(W.SEEDS["uniform"], 0, n, device=dev)
+    keys0 = ((r >> 32) & 0xFFFFFFFF).to(torch.int64).to(torch.int32) if kb == 4 else r
+    del r
+    vals0 = torch.arange(n, dtype=torch.int32, device=dev)
+    if layout:
+        bs, pc, lay = 0, 0, layout
+    else:
+        bs, pc, lay = R.radsort_plan_default(n, kb, 4, db)
+    wsb = R.radsort_workspace_size(n, kb, 4, db, 0, 0, layout)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
+    free_b = torch.cuda.mem_get_info(dev)[0]
+    nbuf = int(max(2, min(steps + warmup, (free_b * 0.4) // (n * E))))
+    kbufs = [torch.empty_like(keys0) for _ in range(nbuf)]
+    vbufs = [torch.empty_like(vals0) for _ in range(nbuf)]
+
+    def refill(i):
+        kbufs[i].copy_(keys0)
+        vbufs[i].copy_(vals0)
+
+    def run(fn):
+        for i in range(nbuf):
+            refill(i)
+        for i in range(warmup):
+            fn(i % nbuf)
+        for i in range(min(warmup, nbuf)):
+            refill(i)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(steps):
+            i = warmup + s
+            if i >= nbuf and s > 0:
+                refill(i % nbuf)
+            fn(i % nbuf)
+        e1.record(stream)
+        barrier()
+        R.radsort_device_status()
+        return e0.elapsed_time(e1) / steps
+
+    R.radsort_trace_read()
+    R.radsort_trace_enable(True)
+    ms = run(lambda i: R.sort_tensors(kbufs[i], vbufs[i], digit_bits=db, workspace=ws, layout=layout))
+    R.radsort_trace_enable(False)
+    recs = R.radsort_trace_read()
+    # the last step's result: sorted and a stable permutation of the input
+    last = (warmup + steps - 1) % nbuf
+    k = kbufs[last].to(torch.int64) & 0xFFFFFFFF if kb == 4 else kbufs[last] ^ (-(2 ** 63))
+    v = vbufs[last].to(torch.int64) & 0xFFFFFFFF
+    eq = kbufs[last][1:] == kbufs[last][:-1]
+    ok = bool((k[1:] >= k[:-1]).all()) and bool(torch.equal(keys0[v], kbufs[last])) and bool(
+        (v[1:][eq] > v[:-1][eq]).all())
+    del k, v, eq
+    rounds = [t for ph, rd, t in recs if ph == "sortPhase"]
+    fin = [t for ph, rd, t in recs if ph == "Finalize"]
+    avg_round = statistics.mean(rounds) if rounds else float("nan")
+    hbm, src = peaks()
+    val = n / (ms / 1e3) / 1e9
+    oms = oval = None
+    if with_oop:
+        ka, va = torch.empty_like(keys0), torch.empty_like(vals0)
+        oms = run(lambda i: R.lsd_oop_tensors(kbufs[i], vbufs[i], ka, va, digit_bits=db))
+        oval = n / (oms / 1e3) / 1e9
+        del ka, va
+    out = {
+        "workload": f"radsort_{'u32' if kb == 4 else 'u64'}_keys_u32_index_2^{log2n}_uniform_d{db}"
+                    + (f"_{layout}" if layout else ""),
+        "n": n, "value": round(val, 3), "unit": "Gkeys/s", "ms_per_step": round(ms, 3), "steps": steps,
+        "block_size": bs, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
+        "round_ms": round(avg_round, 4),
+        "round_frac": round((n * 2 * E) / (avg_round / 1e3) / 1e9 / hbm, 4),
+        "finalize_ms": round(statistics.mean(fin), 4) if fin else None,
+        "result_checked": ok,
+        "oop": None if oval is None else {
+            "value": round(oval, 3), "ms_per_step": round(oms, 3),
+            "extra_bytes": n * E + R.radsort_lsd_oop_scratch_size(n, kb, 4, db)},
+        "radsort_over_oop": None if oval is None else round(val / oval, 4),
+    }
+    del kbufs, vbufs, ws, keys0, vals0
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm

@@ -92,7 +92,12 @@ typedef struct {
                             with its own head start of sigma blocks (Sec. 4.3);
                             nonzero with layout AUTO selects the chunk layout */
     uint32_t layout;     /* RADSORT_LAYOUT_* */
-    uint32_t reserved[5];
+    uint32_t shape;      /* grid layout, tile shape of the round kernel:
+                            0 or 1, one CTA of 16 consumer warps per SM on the
+                            largest tiles; 2 (8-bit digits), two groups of 8
+                            warps on smaller tiles (4096 or 8192 elements),
+                            for arrays of few tiles per SM */
+    uint32_t reserved[4];
 } radsort_plan;
 
 /* Human-readable name of a status code (static storage). */
@@ -107,7 +112,8 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
  * of keys[0..n) (and values, if not NULL) under every plan of the automatic
  * plan's layout whose workspace fits the same budget (2% of the arrays, or
  * 1.25x the least workspace of any block size), and returns the fastest in
- * *plan.  Grid layout: block sizes 256 .. 4096 that a tile holds whole; chunk
+ * *plan.  Grid layout: block sizes 256 .. 4096 that a tile holds whole, with
+ * both tile shapes (radsort_plan.shape 0 and 2) for 8-bit digits; chunk
  * layout: the automatic chunk count with block sizes 256 .. 2048.  Arrays up
  * to RADSORT_SCRATCH_MAX_N get the out-of-place plan without timing.
  * keys and values are read, never written (each timed sort starts from a
@@ -121,6 +127,16 @@ radsort_status radsort_plan_default(size_t n, int key_bytes, int value_bytes, in
  */
 radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t n, int key_bytes,
                                 int digit_bits, void *stream, radsort_plan *plan);
+
+/*
+ * radsort_autotune for both digit widths: tunes (or takes from the cache)
+ * the plan for 8-bit and for 11-bit digits and returns the faster width in
+ * *digit_bits with its plan (8 when the arrays are small enough that neither
+ * is timed).  Pass both to radsort_sort_ex.  Same arguments, allocation,
+ * synchronisation and errors as radsort_autotune.
+ */
+radsort_status radsort_autotune_digits(const void *keys, const uint32_t *values, size_t n, int key_bytes,
+                                       void *stream, int *digit_bits, radsort_plan *plan);
 
 /*
  * Bytes of device workspace radsort_sort_ex needs: the scratch array T
@@ -282,6 +298,18 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
                                       const uint64_t *offsets_host, size_t num_segments,
                                       int key_bytes, int digit_bits, void *workspace,
                                       size_t workspace_bytes, void *stream);
+
+/*
+ * Autotuner of the batched sort (no counterpart in the paper): times
+ * radsort_sort_segmented on a device copy of keys / values (not modified)
+ * with 8- and 11-bit digits, twice each, and returns the faster width in
+ * *digit_bits.  Allocates the copy and the larger workspace stream-ordered
+ * and waits for `stream`.  EINVAL on a bad width, NULL pointers or
+ * unaligned arrays; a failed timed sort returns its status.
+ */
+radsort_status radsort_segmented_autotune(const void *keys, const uint32_t *values, const uint64_t *offsets_dev,
+                                         const uint64_t *offsets_host, size_t num_segments, int key_bytes,
+                                         void *stream, int *digit_bits);
 
 /*
  * Comparison baseline for the batched sort: the same segments, the same

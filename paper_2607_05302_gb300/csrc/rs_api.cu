@@ -144,15 +144,18 @@ static radsort_status fill_geom(size_t n, int kb, bool hasv, int db, uint32_t b,
     g->G = static_cast<uint32_t>(H);
     g->grid = false;
     g->msd = false;
+    g->shape = 0;
     return RADSORT_OK;
 }
 
 // Geometry of the grid layout (one chain per bucket on the output block
 // grid): head start (GRID_AHEAD + 2)*sigma, scratch H + 1 blocks (the last
 // holds the input tail), the data in logical blocks H .. H + nA.
-static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32_t b, Geom *g)
+static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32_t b, int shape, Geom *g)
 {
-    if (!pow2(b) || b < 64 || b > 4096 || lb_tile(kb, db, hasv) % b != 0)
+    if (shape < 0 || shape > 2)
+        return RADSORT_EINVAL;
+    if (!pow2(b) || b < 64 || b > 4096 || lb_tile(kb, db, hasv, shape) % b != 0)
         return RADSORT_EINVAL; // a tile holds whole blocks
     if (n >= (size_t(1) << 31))
         return RADSORT_EINVAL; // look-back words hold 31-bit prefixes
@@ -167,6 +170,7 @@ static radsort_status fill_geom_grid(size_t n, int kb, bool hasv, int db, uint32
     g->p = 1;
     g->grid = true;
     g->msd = false;
+    g->shape = shape;
     const unsigned long long nA = n / b;
     const unsigned long long H = (GRID_AHEAD + 2ull) * g->sigma;
     const unsigned long long npi = nA + H + 1;
@@ -201,7 +205,7 @@ static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
         size_t least = 0;
         for (int i = 0; i < 5; ++i) {
             Geom g;
-            if (fill_geom_grid(n, kb, vb != 0, db, cands[i], &g) != RADSORT_OK)
+            if (fill_geom_grid(n, kb, vb != 0, db, cands[i], 0, &g) != RADSORT_OK)
                 continue;
             ws[i] = layout(g, nullptr, nullptr);
             if (!least || ws[i] < least)
@@ -320,7 +324,7 @@ static radsort_status make_geom(size_t n, int kb, bool hasv, int db, const radso
     if (plan && plan->block_size)
         pl.block_size = plan->block_size;
     if (pl.layout == RADSORT_LAYOUT_GRID)
-        return fill_geom_grid(n, kb, hasv, db, pl.block_size, g);
+        return fill_geom_grid(n, kb, hasv, db, pl.block_size, plan ? static_cast<int>(plan->shape) : 0, g);
     if (plan && plan->num_chunks)
         pl.num_chunks = plan->num_chunks;
     return fill_geom(n, kb, hasv, db, pl.block_size, pl.num_chunks, g);
@@ -501,13 +505,14 @@ namespace {
 struct TuneEntry {
     int dev, lg, kb, vb, db;
     radsort_plan plan;
+    float ms; // its timed sort (-1: chosen without timing)
 };
 constexpr int TUNE_CAP = 256;
 std::mutex g_tune_mu;
 TuneEntry g_tune[TUNE_CAP];
 int g_tune_n = 0;
 
-constexpr int MAX_CANDS = 8;
+constexpr int MAX_CANDS = 16;
 struct Cands {
     radsort_plan p[MAX_CANDS];
     int n = 0;
@@ -525,25 +530,32 @@ Cands tune_candidates(size_t n, int kb, int vb, int db, const radsort_plan &base
     Cands out;
     const double two = 0.02 * double(n) * double(kb + vb);
     if (base.layout == RADSORT_LAYOUT_GRID) {
+        // block sizes x tile shapes (the second shape where it differs)
         const uint32_t cands[] = {256, 512, 1024, 2048, 4096};
-        size_t ws[5] = {}, least = 0;
-        for (int i = 0; i < 5; ++i) {
-            Geom g;
-            if (fill_geom_grid(n, kb, vb != 0, db, cands[i], &g) != RADSORT_OK)
+        const int shapes[] = {0, 2};
+        for (int sh : shapes) {
+            if (sh && !lb_shape_differs(db, sh))
                 continue;
-            ws[i] = layout(g, nullptr, nullptr);
-            if (!least || ws[i] < least)
-                least = ws[i];
-        }
-        const double budget = two > 1.25 * double(least) ? two : 1.25 * double(least);
-        for (int i = 0; i < 5; ++i)
-            if (ws[i] && double(ws[i]) <= budget) {
-                radsort_plan p{};
-                p.layout = RADSORT_LAYOUT_GRID;
-                p.block_size = cands[i];
-                p.num_chunks = 1;
-                out.push_back(p);
+            size_t ws[5] = {}, least = 0;
+            for (int i = 0; i < 5; ++i) {
+                Geom g;
+                if (fill_geom_grid(n, kb, vb != 0, db, cands[i], sh, &g) != RADSORT_OK)
+                    continue;
+                ws[i] = layout(g, nullptr, nullptr);
+                if (!least || ws[i] < least)
+                    least = ws[i];
             }
+            const double budget = two > 1.25 * double(least) ? two : 1.25 * double(least);
+            for (int i = 0; i < 5; ++i)
+                if (ws[i] && double(ws[i]) <= budget) {
+                    radsort_plan p{};
+                    p.layout = RADSORT_LAYOUT_GRID;
+                    p.block_size = cands[i];
+                    p.num_chunks = 1;
+                    p.shape = static_cast<uint32_t>(sh);
+                    out.push_back(p);
+                }
+        }
     } else {
         const double budget = two > double(workspace_of(n, kb, vb, db, base)) ? two
                                                                            : double(workspace_of(n, kb, vb, db, base));
@@ -737,13 +749,13 @@ radsort_status radsort_sort_ex(void *keys, uint32_t *values, size_t n, int key_b
 }
 
 
-radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t n, int key_bytes,
-                                int digit_bits, void *stream, radsort_plan *plan)
+} // extern "C"
+
+// The fastest plan for one digit width, and its time (-1 if not timed).
+static radsort_status tune_one(const void *keys, const uint32_t *values, size_t n, int key_bytes, int digit_bits,
+                               void *stream, radsort_plan *plan, float *out_ms)
 {
-    if (!plan || (key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
-        return RADSORT_EINVAL;
-    if (n > 1 && (!keys || !aligned16(keys) || (values && !aligned16(values))))
-        return RADSORT_EINVAL;
+    *out_ms = -1.f;
     const int vb = values ? 4 : 0;
     radsort_plan base{};
     radsort_status s = radsort_plan_default(n < 2 ? 2 : n, key_bytes, vb, digit_bits, &base);
@@ -766,6 +778,7 @@ radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t
                 g_tune[i].db == digit_bits && g_tune[i].plan.layout == base.layout &&
                 workspace_of(n, key_bytes, vb, digit_bits, g_tune[i].plan)) {
                 *plan = g_tune[i].plan;
+                *out_ms = g_tune[i].ms;
                 return RADSORT_OK;
             }
     }
@@ -844,9 +857,43 @@ radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t
         if (slot < 0 && g_tune_n < TUNE_CAP)
             slot = g_tune_n++;
         if (slot >= 0)
-            g_tune[slot] = TuneEntry{dev, lg, key_bytes, vb, digit_bits, best};
+            g_tune[slot] = TuneEntry{dev, lg, key_bytes, vb, digit_bits, best, best_ms};
     }
     *plan = best;
+    *out_ms = best_ms;
+    return RADSORT_OK;
+}
+
+extern "C" {
+
+radsort_status radsort_autotune(const void *keys, const uint32_t *values, size_t n, int key_bytes,
+                                int digit_bits, void *stream, radsort_plan *plan)
+{
+    if (!plan || (key_bytes != 4 && key_bytes != 8) || (digit_bits != 8 && digit_bits != 11))
+        return RADSORT_EINVAL;
+    if (n > 1 && (!keys || !aligned16(keys) || (values && !aligned16(values))))
+        return RADSORT_EINVAL;
+    float ms;
+    return tune_one(keys, values, n, key_bytes, digit_bits, stream, plan, &ms);
+}
+
+radsort_status radsort_autotune_digits(const void *keys, const uint32_t *values, size_t n, int key_bytes,
+                                       void *stream, int *digit_bits, radsort_plan *plan)
+{
+    if (!plan || !digit_bits || (key_bytes != 4 && key_bytes != 8))
+        return RADSORT_EINVAL;
+    if (n > 1 && (!keys || !aligned16(keys) || (values && !aligned16(values))))
+        return RADSORT_EINVAL;
+    radsort_plan p8{}, p11{};
+    float m8, m11;
+    radsort_status s = tune_one(keys, values, n, key_bytes, 8, stream, &p8, &m8);
+    if (s == RADSORT_OK)
+        s = tune_one(keys, values, n, key_bytes, 11, stream, &p11, &m11);
+    if (s != RADSORT_OK)
+        return s;
+    const bool eleven = m8 >= 0.f && m11 >= 0.f && m11 < m8;
+    *digit_bits = eleven ? 11 : 8;
+    *plan = eleven ? p11 : p8;
     return RADSORT_OK;
 }
 
@@ -1119,6 +1166,79 @@ radsort_status radsort_lsd_oop_segmented_workspace_size(const uint64_t *offsets_
     SegPlan sp;
     radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, true, &sp);
     *bytes = s == RADSORT_OK ? sp.total : 0;
+    return s;
+}
+
+radsort_status radsort_segmented_autotune(const void *keys, const uint32_t *values, const uint64_t *offsets_dev,
+                                         const uint64_t *offsets_host, size_t num_segments, int key_bytes,
+                                         void *stream, int *digit_bits)
+{
+    if (!digit_bits || (key_bytes != 4 && key_bytes != 8) || (num_segments && (!offsets_host || !offsets_dev)))
+        return RADSORT_EINVAL;
+    *digit_bits = 8;
+    if (num_segments == 0)
+        return RADSORT_OK;
+    if (!keys || !aligned16(keys) || (values && !aligned16(values)))
+        return RADSORT_EINVAL;
+    const bool hasv = values != nullptr;
+    const size_t n = offsets_host[num_segments] - offsets_host[0];
+    SegPlan s8, s11;
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 8, false, &s8);
+    if (s == RADSORT_OK)
+        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 11, false, &s11);
+    if (s != RADSORT_OK)
+        return s;
+    const size_t end = offsets_host[num_segments];
+    const size_t kbytes = align_up(end * key_bytes, 256), vbytes = hasv ? align_up(end * 4, 256) : 0;
+    const size_t wsb = s8.total > s11.total ? s8.total : s11.total;
+    cudaStream_t st = as_stream(stream);
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&buf), kbytes + vbytes + wsb + 256, st);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    float best[2] = {-1.f, -1.f};
+    for (int w = 0; w < 2 && e == cudaSuccess && s == RADSORT_OK && n > 1; ++w) {
+        const int db = w ? 11 : 8;
+        for (int rep = 0; rep < 2 && e == cudaSuccess && s == RADSORT_OK; ++rep) {
+            e = cudaMemcpyAsync(buf, keys, end * key_bytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess && hasv)
+                e = cudaMemcpyAsync(buf + kbytes, values, end * 4, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaEventRecord(e0, st);
+            if (e != cudaSuccess)
+                break;
+            s = radsort_sort_segmented(buf, hasv ? reinterpret_cast<uint32_t *>(buf + kbytes) : nullptr, offsets_dev,
+                                       offsets_host, num_segments, key_bytes, db, buf + kbytes + vbytes, wsb,
+                                       stream);
+            if (s != RADSORT_OK)
+                break;
+            e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess)
+                e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && (best[w] < 0.f || ms < best[w]))
+                best[w] = ms;
+        }
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    if (s == RADSORT_OK && e != cudaSuccess)
+        s = cuda_status(e);
+    if (s == RADSORT_OK)
+        s = radsort_device_status(stream);
+    if (s == RADSORT_OK && ef != cudaSuccess)
+        s = cuda_status(ef);
+    if (s == RADSORT_OK && best[0] >= 0.f && best[1] >= 0.f && best[1] < best[0])
+        *digit_bits = 11;
     return s;
 }
 

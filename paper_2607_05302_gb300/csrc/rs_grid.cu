@@ -1299,15 +1299,34 @@ template <typename F> static cudaError_t lb_dispatch(int kb, int db, bool hasv, 
                 : f.template operator()<u64, false, 11, 8192, 16, 1, 2>();
 }
 
+// Radsort rounds with a tile shape: 0 or 1, the configuration above; 2 (8-bit
+// digits), two groups of 8 warps on smaller tiles with two stages each, which
+// the autotuner may pick where the arrays hold few tiles per SM
+template <typename F> static cudaError_t lb_dispatch_shape(int kb, int db, bool hasv, int shape, F &&f)
+{
+    using u64 = unsigned long long;
+    if (shape == 2 && db == 8) {
+        if (kb == 4)
+            return hasv ? f.template operator()<uint32_t, true, 8, 4096, 8, 2, 4>()
+                        : f.template operator()<uint32_t, false, 8, 8192, 8, 2, 4>();
+        return hasv ? f.template operator()<u64, true, 8, 4096, 8, 2, 2>()
+                    : f.template operator()<u64, false, 8, 4096, 8, 2, 4>();
+    }
+    return lb_dispatch(kb, db, hasv, f);
+}
+
 } // namespace
 
-uint32_t lb_tile(int kb, int db, bool hasv)
+bool lb_shape_differs(int db, int shape) { return shape == 2 && db == 8; }
+
+uint32_t lb_tile(int kb, int db, bool hasv, int shape)
 {
     uint32_t r = 0;
-    lb_dispatch(kb, db, hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
-        r = TILE;
-        return cudaSuccess;
-    });
+    lb_dispatch_shape(kb, db, hasv, shape,
+                      [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
+                          r = TILE;
+                          return cudaSuccess;
+                      });
     return r;
 }
 
@@ -1336,7 +1355,7 @@ static size_t ring_bytes(size_t ntiles, uint32_t sigma)
 
 size_t grid_ring_bytes(const Geom &g)
 {
-    const uint32_t tile = lb_tile(g.kb, g.db, g.hasv);
+    const uint32_t tile = lb_tile(g.kb, g.db, g.hasv, g.shape);
     return ring_bytes((g.n + tile - 1) / tile, g.sigma);
 }
 
@@ -1391,7 +1410,8 @@ cudaError_t launch_grid_round(const Geom &g, const Bufs &w, const uint32_t *pi, 
                               int round, cudaStream_t st)
 {
     const uint32_t n = static_cast<uint32_t>(g.n);
-    return lb_dispatch(g.kb, g.db, g.hasv, [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
+    return lb_dispatch_shape(g.kb, g.db, g.hasv, g.shape,
+                             [&]<typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES>() {
         using C = LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, false>;
         const size_t ntiles = (g.n + TILE - 1) / TILE;
         const int grid = lb_ctas<KT, HASV, DB, TILE, NW, NG, STAGES, false>(ntiles);
@@ -1430,7 +1450,7 @@ size_t lsd_oop_scratch_bytes(size_t n, int kb, int db, bool hasv)
 {
     const size_t sigma = size_t(1) << db;
     const int nt = (8 * kb + db - 1) / db;
-    const uint32_t tile = lb_tile(kb, db, hasv);
+    const uint32_t tile = lb_tile(kb, db, hasv, 0);
     const size_t ntiles = (n + tile - 1) / tile;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     return al(nt * sigma * 4) + al(nt * (sigma + 1) * 4) + al(ring_bytes(ntiles, uint32_t(sigma))) + al(64 * 4);
@@ -1452,7 +1472,7 @@ cudaError_t launch_lsd_oop_ws(void *keys, uint32_t *vals, void *keys_alt, uint32
     if (e != cudaSuccess)
         return e;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const uint32_t tile = lb_tile(kb, db, vals != nullptr);
+    const uint32_t tile = lb_tile(kb, db, vals != nullptr, 0);
     const size_t ntiles = (n + tile - 1) / tile;
     uint32_t *hist = reinterpret_cast<uint32_t *>(scr);
     uint32_t *off = reinterpret_cast<uint32_t *>(scr + al(nt * sigma * 4));

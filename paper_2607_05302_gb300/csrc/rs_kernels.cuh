@@ -31,6 +31,7 @@ struct Geom {
     uint32_t G;        // groups (bucket, chunk) = sigma*p
     bool grid;         // one chain per bucket on the output block grid (H = (GRID_AHEAD + 2) sigma, nT = H + 1)
     bool msd;          // chunk layout with p = sigma: a split on the top digit, then each bucket on its own
+    int shape;         // grid layout: tile shape of the round kernel (radsort_plan.shape)
 };
 
 // Device buffers of one sort, carved from one workspace allocation.
@@ -83,8 +84,10 @@ cudaError_t launch_grid_prep(const Geom &g, const Bufs &w, const uint32_t *pi, u
 cudaError_t launch_grid_round(const Geom &g, const Bufs &w, const uint32_t *pi, uint32_t *pin,
                               int round, cudaStream_t st);
 size_t grid_ring_bytes(const Geom &g); // look-back ring of the grid layout
-// elements per tile of the look-back round kernel
-uint32_t lb_tile(int kb, int db, bool hasv);
+// elements per tile of the look-back round kernel with a tile shape (0: the
+// default), and whether a shape differs from the default for the digit width
+uint32_t lb_tile(int kb, int db, bool hasv, int shape);
+bool lb_shape_differs(int db, int shape);
 // gather of the logical sequence (Sec. 4.1 iterator)
 cudaError_t launch_gather(const Geom &g, const Bufs &w, const uint32_t *pi, void *out_k,
                           uint32_t *out_v, cudaStream_t st);

@@ -40,7 +40,7 @@ PHASES = {0: "setup", 1: "sortPhase", 2: "fixupPhase", 3: "Finalize", 4: "key_tr
 
 class Plan(ctypes.Structure):
     _fields_ = [("block_size", ctypes.c_uint32), ("num_chunks", ctypes.c_uint32),
-                ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("layout", ctypes.c_uint32), ("shape", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
 
 
 _lib = None
@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
             "radsort_status_str": ([i], ctypes.c_char_p),
             "radsort_plan_default": ([sz, i, i, i, pplan], i),
             "radsort_autotune": ([vp, vp, sz, i, i, vp, pplan], i),
+            "radsort_autotune_digits": ([vp, vp, sz, i, vp, ctypes.POINTER(i), pplan], i),
+            "radsort_segmented_autotune": ([vp, vp, vp, vp, sz, i, vp, ctypes.POINTER(i)], i),
             "radsort_workspace_size": ([sz, i, i, i, pplan, ctypes.POINTER(sz)], i),
             "radsort_sort": ([vp, vp, sz, i, i, vp], i),
             "radsort_sort_noalloc": ([vp, vp, sz, i, i, vp], i),
@@ -98,7 +100,8 @@ def lib() -> ctypes.CDLL:
 
 
 # exported names declared in include/radsort.h
-EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_autotune", "radsort_workspace_size", "radsort_sort",
+EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_autotune", "radsort_autotune_digits",
+           "radsort_segmented_autotune", "radsort_workspace_size", "radsort_sort",
            "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_sort_segmented",
            "radsort_lsd_oop_segmented_workspace_size", "radsort_lsd_oop_sort_segmented",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
@@ -122,14 +125,15 @@ def _layout(layout):
     return LAYOUTS[layout] if isinstance(layout, str) else int(layout)
 
 
-def _plan(block_size=0, num_chunks=0, layout=0):
+def _plan(block_size=0, num_chunks=0, layout=0, shape=0):
     layout = _layout(layout)
-    if not block_size and not num_chunks and not layout:
+    if not block_size and not num_chunks and not layout and not shape:
         return None
     p = Plan()
     p.block_size = block_size
     p.num_chunks = num_chunks
     p.layout = layout
+    p.shape = shape
     return ctypes.byref(p)
 
 
@@ -143,19 +147,41 @@ def radsort_plan_default(n, key_bytes, value_bytes, digit_bits):
 
 
 def radsort_autotune(keys, values=None, *, digit_bits=8, stream=None):
-    """(block_size, num_chunks, layout) of the fastest plan for sorting these
-    CUDA tensors (timed on copies; the tensors are not modified)."""
+    """(block_size, num_chunks, layout, shape) of the fastest plan for sorting
+    these CUDA tensors (timed on copies; the tensors are not modified)."""
     p = Plan()
     _ok(lib().radsort_autotune(_ptr(keys), _ptr(values), keys.numel(), _key_bytes(keys), digit_bits,
                                _torch_stream(stream), ctypes.byref(p)), "radsort_autotune")
-    return int(p.block_size), int(p.num_chunks), int(p.layout)
+    return int(p.block_size), int(p.num_chunks), int(p.layout), int(p.shape)
+
+
+def radsort_autotune_digits(keys, values=None, *, stream=None):
+    """(digit_bits, block_size, num_chunks, layout, shape) of the fastest plan
+    over both digit widths (timed on copies)."""
+    p = Plan()
+    d = ctypes.c_int(0)
+    _ok(lib().radsort_autotune_digits(_ptr(keys), _ptr(values), keys.numel(), _key_bytes(keys),
+                                      _torch_stream(stream), ctypes.byref(d), ctypes.byref(p)),
+        "radsort_autotune_digits")
+    return int(d.value), int(p.block_size), int(p.num_chunks), int(p.layout), int(p.shape)
+
+
+def segmented_autotune(keys, values, offsets_dev, offsets_host, *, stream=None):
+    """The faster digit width (8 or 11) for this batch, timed on copies."""
+    import numpy as np
+    oh = np.ascontiguousarray(offsets_host, dtype=np.uint64)
+    d = ctypes.c_int(0)
+    _ok(lib().radsort_segmented_autotune(_ptr(keys), _ptr(values), _ptr(offsets_dev),
+                                         oh.ctypes.data_as(ctypes.c_void_p), oh.size - 1, _key_bytes(keys),
+                                         _torch_stream(stream), ctypes.byref(d)), "radsort_segmented_autotune")
+    return int(d.value)
 
 
 def radsort_workspace_size(n, key_bytes, value_bytes, digit_bits, block_size=0, num_chunks=0,
-                           layout=0):
+                           layout=0, shape=0):
     out = ctypes.c_size_t(0)
     _ok(lib().radsort_workspace_size(n, key_bytes, value_bytes, digit_bits,
-                                     _plan(block_size, num_chunks, layout), ctypes.byref(out)),
+                                     _plan(block_size, num_chunks, layout, shape), ctypes.byref(out)),
         "radsort_workspace_size")
     return int(out.value)
 
@@ -165,9 +191,9 @@ def radsort_sort(keys, values, n, key_bytes, digit_bits, stream):
 
 
 def radsort_sort_ex(keys, values, n, key_bytes, digit_bits, flags=0, block_size=0, num_chunks=0,
-                    workspace=None, workspace_bytes=0, stream=None, layout=0):
+                    workspace=None, workspace_bytes=0, stream=None, layout=0, shape=0):
     _ok(lib().radsort_sort_ex(keys, values, n, key_bytes, digit_bits, flags,
-                              _plan(block_size, num_chunks, layout), workspace, workspace_bytes,
+                              _plan(block_size, num_chunks, layout, shape), workspace, workspace_bytes,
                               stream),
         "radsort_sort_ex")
 
@@ -247,7 +273,7 @@ def _ptr(t):
 
 
 def sort_tensors(keys, values=None, *, digit_bits=8, float_keys=False, block_size=0, num_chunks=0,
-                 workspace=None, stream=None, layout=0):
+                 workspace=None, stream=None, layout=0, shape=0):
     """In-place stable Radsort of CUDA tensors (keys: 32/64-bit, read as
     unsigned; values: optional 32-bit)."""
     assert keys.is_cuda and keys.is_contiguous()
@@ -258,7 +284,7 @@ def sort_tensors(keys, values=None, *, digit_bits=8, float_keys=False, block_siz
     ws, wsb = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel() * workspace.element_size())
     radsort_sort_ex(_ptr(keys), _ptr(values), n, _key_bytes(keys), digit_bits,
                     RADSORT_KEY_FLOAT32 if float_keys else 0, block_size, num_chunks, ws, wsb,
-                    _torch_stream(stream), layout)
+                    _torch_stream(stream), layout, shape)
 
 
 def sort_rounds_tensors(keys, values, rounds, out_keys, out_values=None, *, digit_bits=8,

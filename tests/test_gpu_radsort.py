@@ -22,11 +22,11 @@ def from_dev(t, dtype):
     return t.cpu().numpy().view(dtype)
 
 
-def gpu_sort(keys, vals, digit_bits=8, float_keys=False, block_size=0, num_chunks=0, layout=0):
+def gpu_sort(keys, vals, digit_bits=8, float_keys=False, block_size=0, num_chunks=0, layout=0, shape=0):
     kt = to_dev(keys)
     vt = None if vals is None else to_dev(vals)
     R.sort_tensors(kt, vt, digit_bits=digit_bits, float_keys=float_keys, block_size=block_size,
-                   num_chunks=num_chunks, layout=layout)
+                   num_chunks=num_chunks, layout=layout, shape=shape)
     R.radsort_device_status()
     return from_dev(kt, keys.dtype), (None if vt is None else from_dev(vt, np.uint32))
 
@@ -311,16 +311,16 @@ def test_autotune_plan_sorts_and_inputs_untouched(kb, db):
     keys = W.make_keys("uniform", n, 8 * kb)
     vals = W.index_payload(n)
     kt, vt = to_dev(keys), to_dev(vals)
-    b, p, lay = R.radsort_autotune(kt, vt, digit_bits=db)
+    b, p, lay, sh = R.radsort_autotune(kt, vt, digit_bits=db)
     R.radsort_device_status()
     assert np.array_equal(from_dev(kt, keys.dtype), keys)
     assert np.array_equal(from_dev(vt, np.uint32), vals)
     assert lay == R.radsort_plan_default(n, kb, 4, db)[2]
-    assert R.radsort_workspace_size(n, kb, 4, db, b, p, lay) > 0
+    assert R.radsort_workspace_size(n, kb, 4, db, b, p, lay, sh) > 0
     t0 = time.perf_counter()
-    assert R.radsort_autotune(kt, vt, digit_bits=db) == (b, p, lay)
+    assert R.radsort_autotune(kt, vt, digit_bits=db) == (b, p, lay, sh)
     assert time.perf_counter() - t0 < 0.05
-    gk, gv = gpu_sort(keys, vals, digit_bits=db, block_size=b, num_chunks=p, layout=lay)
+    gk, gv = gpu_sort(keys, vals, digit_bits=db, block_size=b, num_chunks=p, layout=lay, shape=sh)
     ek, ev = oracle_sort(keys, vals, 8 * kb, db)
     assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
 
@@ -368,3 +368,37 @@ def test_msd_split_rejects_11_bit_digits():
     kt = torch.zeros(1000, dtype=torch.int32, device=DEV)
     with pytest.raises(R.RadsortError):
         R.sort_tensors(kt, None, digit_bits=11, layout="msd")
+
+
+@pytest.mark.parametrize("kb,with_vals,bs", [(4, True, 256), (4, True, 4096), (4, False, 1024), (8, True, 512),
+                                             (8, False, 2048)])
+@pytest.mark.parametrize("n", [3, 4097, 65543, 300001, 1 << 20])
+def test_tile_shape_two_groups(n, kb, with_vals, bs):
+    """The round kernel's second tile shape (two groups of 8 consumer warps
+    on smaller tiles): bit-exact against the oracle."""
+    rng = np.random.default_rng(n + bs)
+    keys = W.make_keys("uniform", n, 8 * kb)
+    keys[::4] = keys[n // 2]
+    vals = W.index_payload(n)
+    gk, gv = gpu_sort(keys, vals if with_vals else None, block_size=bs, layout="grid", shape=2)
+    ek, ev = oracle_sort(keys, vals, 8 * kb, 8)
+    assert np.array_equal(gk, ek)
+    if with_vals:
+        assert np.array_equal(gv, ev)
+
+
+@pytest.mark.parametrize("kb", [4, 8])
+def test_autotune_digit_width(kb):
+    """radsort_autotune_digits returns a width and a plan whose sort matches
+    the oracle; the arrays are left as they were."""
+    n = (1 << 21) + 5
+    keys = W.make_keys("uniform", n, 8 * kb)
+    vals = W.index_payload(n)
+    kt, vt = to_dev(keys), to_dev(vals)
+    db, b, p, lay, sh = R.radsort_autotune_digits(kt, vt)
+    R.radsort_device_status()
+    assert db in (8, 11)
+    assert np.array_equal(from_dev(kt, keys.dtype), keys)
+    gk, gv = gpu_sort(keys, vals, digit_bits=db, block_size=b, num_chunks=p, layout=lay, shape=sh)
+    ek, ev = oracle_sort(keys, vals, 8 * kb, db)
+    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)

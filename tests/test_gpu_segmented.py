@@ -197,3 +197,20 @@ def test_captured_graph_with_long_segments():
         R.radsort_device_status()
         assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
         assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
+def test_segmented_autotune_leaves_inputs_and_picks_a_width():
+    lens = [int(x) for x in LENGTH_SETS["mixed"]]
+    off = offsets_of(lens)
+    n = int(off[-1])
+    keys = W.make_keys("uniform", n)
+    kt = torch.from_numpy(keys.view(np.int32)).to(DEV)
+    vt = torch.arange(n, dtype=torch.int32, device=DEV)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    db = R.segmented_autotune(kt, vt, od, off)
+    assert db in (8, 11)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), keys)
+    kt2, vt2, _ = run_segmented(keys, lens, db)
+    ek, ev = oracle_segmented_u32(keys, lens, db)
+    assert np.array_equal(kt2.cpu().numpy().view(np.uint32), ek)
+    assert np.array_equal(vt2.cpu().numpy().view(np.uint32), ev)

@@ -73,3 +73,18 @@ def test_profiled_traffic_follows_the_kernel_sources(monkeypatch):
     assert bench.profiled_traffic(n, 4, 11, "grid", 2048, text=txt) is None
     monkeypatch.setattr(bench, "round_kernel_hash", lambda files: "0" * 16)
     assert bench.profiled_traffic(n, 4, 8, "grid", 2048, text=txt) is None
+
+
+def test_bench_defines_every_leg():
+    """The helpers bench.py's GPU arm calls are defined (a guard for edits
+    that drop one: the GPU arm runs only on a GPU)."""
+    import ast
+
+    import bench
+
+    tree = ast.parse(open(os.path.join(bench.ROOT, "bench.py")).read())
+    called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
+    defined = {n.name for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)}
+    import builtins
+    missing = {c for c in called if c not in defined and not hasattr(builtins, c)}
+    assert not missing, missing
