@@ -84,7 +84,9 @@ def test_bench_defines_every_leg():
 
     tree = ast.parse(open(os.path.join(bench.ROOT, "bench.py")).read())
     called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
-    defined = {n.name for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)}
+    defined = {n.name for n in ast.walk(tree) if isinstance(n, (ast.FunctionDef, ast.ClassDef))}
+    defined |= {n.arg for n in ast.walk(tree) if isinstance(n, ast.arg)}  # callables passed in
+    defined |= {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Store)}
     import builtins
     missing = {c for c in called if c not in defined and not hasattr(builtins, c)}
     assert not missing, missing
