@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-oop", action="store_true", help="skip the out-of-place comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the short serving run (200 requests) in the default line")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (2^28 u32, 2^30 u64 with 8- and 11-bit digits)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -544,7 +546,7 @@ def main():
     if a.workload == "serve":
         from paper_2607_05302_gb300 import serve
 
-        print(json.dumps(serve.run_bench(steps=a.steps)), flush=True)
+        print(json.dumps(serve.run_bench(steps=a.steps, tight_cap=16 * 10 ** 9)), flush=True)
         return
 
     import numpy as np
@@ -754,6 +756,18 @@ def main():
             time_workload(R, W, dev, a.log2n, kb, db, min(a.steps, 6), max(3, min(a.warmup, 3)), barrier,
                           stream, layout="msd", with_oop=False) if db == 8 else None)
 
+    # ---- a short serving run (config 5, 200 requests), both methods
+    serve_line = None
+    if not a.no_serve and world == 1:
+        from paper_2607_05302_gb300 import serve
+
+        torch.cuda.empty_cache()
+        sv = serve.run_bench(steps=200)
+        serve_line = {"requests": 200, "cap_bytes": sv["config"]["cap_bytes"],
+                      **{m: {k: (round(v, 3) if isinstance(v, float) else v) for k, v in sv[m].items()
+                             if k in ("p50_ms", "p99_ms", "keys_per_s", "peak_concurrency", "peak_bytes")}
+                         for m in ("radsort", "oop")}}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         rate, sample, el = oracle_sample_rate(a, a.cpu_seconds)
@@ -774,7 +788,7 @@ def main():
                        "extra": "uniform keys, automatic plan, comparator beside each; fresh copies per step"},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
-            "oop": oop, "chunk_layout": plan2, "extra": extra,
+            "oop": oop, "chunk_layout": plan2, "extra": extra, "serve": serve_line,
             "phases_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
             "algorithmic_bytes_per_step": step_bytes,
         }
