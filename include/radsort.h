@@ -341,8 +341,11 @@ radsort_status radsort_lsd_oop_sort_segmented(void *keys, uint32_t *values, void
  * exits).  The plan is the automatic one (grid layout) when its workspace
  * fits, else the chunk layout with block size 256 and as many chunks (up to
  * one per SM) as fit; an n whose workspace does not fit even with one chunk
- * returns RADSORT_ENOMEM and enqueues nothing (up to about 1.07e9 elements
- * with 4-byte keys and values fit, 8.8e8 with 8-byte keys).
+ * returns RADSORT_ENOMEM and enqueues nothing.  With 8-bit digits the grid
+ * layout fits up to 2^31 - 1 elements with 4-byte keys (with or without
+ * values) and with 8-byte keys alone, up to 2^30 with 8-byte keys and values;
+ * with 11-bit digits up to 2^30 4-byte keys alone and 2^29 with values or with
+ * 8-byte keys, 2^28 with 8-byte keys and values.
  * Every call looks up the array's device address on the current device with
  * cudaGetSymbolAddress (which allocates nothing), so the address stays right
  * after a context reset; the first call on a device may also load the
