@@ -528,7 +528,12 @@ template <typename KT, bool HASV, int DB, int TILE, int NW, int NG, int STAGES, 
     static constexpr size_t BK_BYTES = al(size_t(3) * SIGMA * 4);
     // touched blocks per tile: at most TILE/b + 2 per bucket with elements
     static constexpr int LIST = MAXM + 2 * (SIGMA < TILE ? SIGMA : TILE) + 2;
-    static constexpr size_t QB_BYTES = al(size_t(SIGMA) * 8);
+    // Radsort with sigma <= 256: per bucket a 16-byte run descriptor (offset,
+    // end of the run's first block, that block's base address) and the list
+    // slot of its first block; otherwise 8 bytes (offset, list slot)
+    static constexpr bool QB16 = !OOP && SMALL;
+    static constexpr size_t QLO_OFF = al(size_t(SIGMA) * (QB16 ? 16 : 8));
+    static constexpr size_t QB_BYTES = QLO_OFF + (QB16 ? al(size_t(SIGMA) * 4) : 0);
     static constexpr size_t LK_BYTES = OOP ? 0 : al(size_t(LIST) * (SMALL ? 8 : 4));
     // sigma = 2048: the per-bucket run offsets and the block list live in
     // the warp-row region, which the tile no longer needs once reordered
@@ -657,6 +662,8 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>
     const uint32_t *ns0 = C::SMALL ? stab : a.tab + SIGMA + 1;
     const uint32_t *ns1 = ns0 + SIGMA, *shr = ns1 + SIGMA;
     uint2 *qb = reinterpret_cast<uint2 *>(gb + C::g_qb);
+    uint4 *qb16 = reinterpret_cast<uint4 *>(gb + C::g_qb);
+    uint32_t *qlo = reinterpret_cast<uint32_t *>(gb + C::g_qb + C::QLO_OFF);
     // list entries: the key block pointer tagged with its array (SMALL), or
     // the block index
     unsigned long long *listk = reinterpret_cast<unsigned long long *>(gb + C::g_lk);
@@ -1135,7 +1142,14 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>
                     continue;
                 const uint32_t g = gpos[c], cn = tcnt[c];
                 const uint32_t l0 = l0s[q], j0 = g >> a.lb;
-                qb[c] = make_uint2(g - bstart[c], l0 - j0);
+                if constexpr (C::QB16) {
+                    // the run's first block is filled in below; an element
+                    // past it reads its block from the list
+                    qb16[c] = make_uint4(g - bstart[c], 0u, 0u, 0u);
+                    qlo[c] = l0 - j0;
+                } else {
+                    qb[c] = make_uint2(g - bstart[c], l0 - j0);
+                }
                 if (!cn || g + cn > sO[c + 1] || g + cn < g)
                     continue; // (a corrupted run was reported in step 4)
                 const uint32_t touched = ((g + cn - 1) >> a.lb) - j0 + 1;
@@ -1173,9 +1187,21 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>
                     if constexpr (C::SMALL) {
                         // one word per entry: the key block pointer, bit 0 set
                         // for a block of A (the value pointer follows from it)
-                        listk[l0 + i] = phys == PI_NONE ? 0ull
-                                                        : (reinterpret_cast<unsigned long long>(kaddr(phys)) |
-                                                           (phys >= a.nT ? 1ull : 0ull));
+                        const unsigned long long w =
+                            phys == PI_NONE ? 0ull
+                                            : (reinterpret_cast<unsigned long long>(kaddr(phys)) |
+                                               (phys >= a.nT ? 1ull : 0ull));
+                        listk[l0 + i] = w;
+                        if (i == 0 && w) {
+                            // the first block as a base for the run's
+                            // positions: key address of position p in it is
+                            // base + p elements (bit 1 marks it valid)
+                            const unsigned long long base =
+                                ((w & ~1ull) - (static_cast<unsigned long long>(j0) << a.lb) * sizeof(KT)) |
+                                (w & 1ull) | 2ull;
+                            qb16[c] = make_uint4(g - bstart[c], (j0 + 1) << a.lb, static_cast<uint32_t>(base),
+                                                 static_cast<uint32_t>(base >> 32));
+                        }
                     } else {
                         listb[l0 + i] = phys;
                     }
@@ -1203,7 +1229,38 @@ __global__ void __launch_bounds__(LbCfg<KT, HASV, DB, TILE, NW, NG, STAGES, OOP>
                     if (HASV)
                         vv = tv[i];
                 }
-                const uint2 qd = qb[digit_of(kv, a.shift, mask)];
+                const uint32_t dg = digit_of(kv, a.shift, mask);
+                if constexpr (C::QB16) {
+                    // Radsort, sigma <= 256: most runs lie in one block, whose
+                    // base address the run descriptor holds; the rest read
+                    // their block from the list
+                    const uint4 qd = qb16[dg];
+                    const uint32_t pos = i + qd.x;
+                    unsigned long long w;
+                    uint32_t idx;
+                    if (pos < qd.y) {
+                        w = (static_cast<unsigned long long>(qd.w) << 32) | qd.z;
+                        idx = pos;
+                    } else {
+                        const uint32_t l = (pos >> a.lb) + qlo[dg];
+                        w = l < TT ? listk[l] : 0ull;
+                        idx = pos & (b - 1);
+                    }
+                    if (w) {
+                        KT *pk = reinterpret_cast<KT *>(w & ~3ull) + idx;
+                        *pk = kv;
+                        if (HASV) {
+                            uint32_t *pv;
+                            if constexpr (sizeof(KT) == 4)
+                                pv = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(pk) + ((w & 1ull) ? dvA : dvT));
+                            else
+                                pv = ((w & 1ull) ? a.Av + (pk - a.Ak) : a.Tv + (pk - a.Tk));
+                            *pv = vv;
+                        }
+                    }
+                    continue;
+                }
+                const uint2 qd = qb[dg];
                 const uint32_t pos = i + qd.x;
                 if constexpr (OOP) {
                     if (pos < a.n) {
