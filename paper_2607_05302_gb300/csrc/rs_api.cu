@@ -933,7 +933,8 @@ constexpr int SEG_STREAMS = 4;
 // Measured on 20,000 lognormal arrays (2^29 keys + values, the longest
 // medium one near 2^18, long segments beside it on the library's streams):
 // 1.5% -> 7.1 Gkeys/s, 3% -> 13.5, 6% -> 24.0, no limit (2 CTAs per SM,
-// 14%) -> 20.7
+// 14%) -> 20.7.  The low-memory plan (8-bit digits) sorts the medium
+// segments in place instead, in a fixed 514 blocks of 32 elements per CTA.
 constexpr double SEG_MED_SHARE = 0.06;
 
 struct SegPlan {
@@ -941,14 +942,17 @@ struct SegPlan {
     size_t large = 0;   // workspace of one long-segment stream
     size_t total = 0;   // base + nstr * large
     uint32_t med_max = 0, med_ctas = 0;
+    bool ip = false;    // the low-memory plan: medium segments in place
     int nstr = 0;       // internal streams used (0: no long segment)
 };
 
 // oop: long segments sorted out of place (Alg. 1) into the caller's
-// alternate arrays, so a stream's slice holds only the comparator's scratch
-radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, bool oop, SegPlan *sp)
+// alternate arrays, so a stream's slice holds only the comparator's scratch;
+// lowmem: medium segments sorted in place (Radsort per CTA; 8-bit digits)
+radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, bool oop, bool lowmem,
+                        SegPlan *sp)
 {
-    size_t large = 0, nlong = 0;
+    size_t large = 0, nlong = 0, nmed = 0;
     uint32_t med_max = 0;
     const uint32_t small_max = seg_small_max(db);
     const size_t n = nseg ? offh[nseg] - offh[0] : 0;
@@ -957,8 +961,11 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
             return RADSORT_EINVAL;
         const size_t len = offh[s + 1] - offh[s];
         if (len <= SEG_MED) {
-            if (len > small_max && len > med_max)
-                med_max = static_cast<uint32_t>(len);
+            if (len > small_max) {
+                ++nmed;
+                if (len > med_max)
+                    med_max = static_cast<uint32_t>(len);
+            }
             continue;
         }
         ++nlong;
@@ -979,8 +986,12 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
             large = (need + 255) / 256 * 256;
     }
     sp->med_max = med_max;
-    sp->med_ctas = seg_med_ctas(med_max, kb, hasv, static_cast<size_t>(SEG_MED_SHARE * double(n) * (kb + (hasv ? 4 : 0))));
-    sp->base = (seg_scratch_bytes(kb, hasv, nseg, med_max, sp->med_ctas) + 255) / 256 * 256;
+    sp->ip = lowmem && !oop && db == 8;
+    sp->med_ctas = !med_max ? 0
+                   : sp->ip ? static_cast<uint32_t>(nmed < seg_ip_ctas() ? nmed : seg_ip_ctas())
+                            : seg_med_ctas(med_max, kb, hasv,
+                                           static_cast<size_t>(SEG_MED_SHARE * double(n) * (kb + (hasv ? 4 : 0))));
+    sp->base = (seg_scratch_bytes(kb, hasv, nseg, med_max, sp->med_ctas, sp->ip) + 255) / 256 * 256;
     sp->large = large;
     sp->nstr = static_cast<int>(nlong < size_t(SEG_STREAMS) ? nlong : size_t(SEG_STREAMS));
     sp->total = sp->base + size_t(sp->nstr) * large;
@@ -1099,8 +1110,23 @@ radsort_status radsort_segmented_workspace_size(const uint64_t *offsets_host, si
         (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
         return RADSORT_EINVAL;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, false, &sp);
     *bytes = s == RADSORT_OK ? sp.total : 0;
+    return s;
+}
+
+radsort_status radsort_segmented_workspace_size_min(const uint64_t *offsets_host, size_t num_segments,
+                                                    int key_bytes, int value_bytes, int digit_bits,
+                                                    size_t *bytes)
+{
+    if (!bytes || (key_bytes != 4 && key_bytes != 8) || (value_bytes != 0 && value_bytes != 4) ||
+        (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
+        return RADSORT_EINVAL;
+    SegPlan fast, lo;
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, false, &fast);
+    if (s == RADSORT_OK)
+        s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, true, &lo);
+    *bytes = s == RADSORT_OK ? (lo.total < fast.total ? lo.total : fast.total) : 0;
     return s;
 }
 
@@ -1119,7 +1145,14 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
         return RADSORT_EINVAL;
     const bool hasv = values != nullptr;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, false, &sp);
+    if (s == RADSORT_OK && workspace && workspace_bytes < sp.total && digit_bits == 8) {
+        // a caller workspace below the fast plan: the low-memory plan if it fits
+        SegPlan lo;
+        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, true, &lo);
+        if (s == RADSORT_OK && workspace_bytes >= lo.total)
+            sp = lo;
+    }
     if (s != RADSORT_OK)
         return s;
     cudaStream_t st = as_stream(stream);
@@ -1130,7 +1163,8 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
         return s;
     auto main = [&]() -> radsort_status {
         return cuda_status(launch_segmented(keys, values, reinterpret_cast<const unsigned long long *>(offsets_dev),
-                                            num_segments, key_bytes, digit_bits, sp.med_max, sp.med_ctas, ws, st));
+                                            num_segments, key_bytes, digit_bits, sp.med_max, sp.med_ctas, sp.ip, ws,
+                                            st));
     };
     radsort_status rs = seg_run(offsets_host, num_segments, sp, static_cast<char *>(ws) + sp.base, st, main,
                       [&](size_t off, size_t len, char *lw, cudaStream_t ls) -> radsort_status {
@@ -1164,7 +1198,7 @@ radsort_status radsort_lsd_oop_segmented_workspace_size(const uint64_t *offsets_
         (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
         return RADSORT_EINVAL;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, true, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, true, false, &sp);
     *bytes = s == RADSORT_OK ? sp.total : 0;
     return s;
 }
@@ -1183,9 +1217,9 @@ radsort_status radsort_segmented_autotune(const void *keys, const uint32_t *valu
     const bool hasv = values != nullptr;
     const size_t n = offsets_host[num_segments] - offsets_host[0];
     SegPlan s8, s11;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 8, false, &s8);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 8, false, false, &s8);
     if (s == RADSORT_OK)
-        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 11, false, &s11);
+        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 11, false, false, &s11);
     if (s != RADSORT_OK)
         return s;
     const size_t end = offsets_host[num_segments];
@@ -1259,7 +1293,7 @@ radsort_status radsort_lsd_oop_sort_segmented(void *keys, uint32_t *values, void
         return RADSORT_EINVAL;
     const bool hasv = values != nullptr;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, true, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, true, false, &sp);
     if (s != RADSORT_OK)
         return s;
     cudaStream_t st = as_stream(stream);
@@ -1270,7 +1304,8 @@ radsort_status radsort_lsd_oop_sort_segmented(void *keys, uint32_t *values, void
         return s;
     auto main = [&]() -> radsort_status {
         return cuda_status(launch_segmented(keys, values, reinterpret_cast<const unsigned long long *>(offsets_dev),
-                                            num_segments, key_bytes, digit_bits, sp.med_max, sp.med_ctas, ws, st));
+                                            num_segments, key_bytes, digit_bits, sp.med_max, sp.med_ctas, sp.ip, ws,
+                                            st));
     };
     radsort_status rs = seg_run(offsets_host, num_segments, sp, static_cast<char *>(ws) + sp.base, st, main,
                       [&](size_t off, size_t len, char *lw, cudaStream_t ls) -> radsort_status {

@@ -112,10 +112,11 @@ size_t lsd_oop_scratch_bytes(size_t n, int kb, int db, bool hasv);
 constexpr uint32_t SEG_MED = 1u << 18;
 uint32_t seg_small_max(int db);
 uint32_t seg_med_ctas(uint32_t med_max, int kb, bool hasv, size_t budget);
-size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg, uint32_t med_max, uint32_t med_ctas);
+uint32_t seg_ip_ctas();
+size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg, uint32_t med_max, uint32_t med_ctas, bool ip);
 cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long long *off_dev,
-                             size_t nseg, int kb, int db, uint32_t med_max, uint32_t med_ctas, void *scratch,
-                             cudaStream_t st);
+                             size_t nseg, int kb, int db, uint32_t med_max, uint32_t med_ctas, bool ip,
+                             void *scratch, cudaStream_t st);
 unsigned take_status_seg();
 
 // devices a process may use (per-device caches are sized for this many)

@@ -7,7 +7,10 @@
 //   * medium (<= SEG_MED): one CTA runs an out-of-place LSD sort between the
 //     segment and its own scratch region.  This is the paper's suggestion of
 //     using the scratch array T as A' of Alg. 1 for arrays smaller than T
-//     (Sec. 5, results);
+//     (Sec. 5, results).  With 8-bit digits and a workspace too small for
+//     those regions, one CTA runs Radsort itself on the segment's own blocks
+//     of 32 elements plus 2 sigma + 2 scratch blocks of its own (Alg. 4-7 on
+//     one processor), a scratch that does not grow with the segments;
 //   * large: the full Radsort path (Alg. 2) on the segment alone.
 // The small and medium classes are listed on the device, and each is
 // processed by one persistent launch that takes segments from an atomic
@@ -136,6 +139,7 @@ struct SegArgs {
     void *scr_k;                   // medium scratch, med_stride elements per CTA
     uint32_t *scr_v;
     uint32_t med_stride;           // the longest medium segment of the call
+    uint32_t med_ip;               // medium segments sorted in place (Radsort per CTA)
     int nt, db;
 };
 
@@ -304,6 +308,544 @@ __global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
     }
 }
 
+// ---- medium segments sorted in place: Radsort on one CTA ----------------
+//
+// The segment is a sequence of logical blocks of IP_B elements; pi[q] names
+// the physical block that holds logical block q: one of the segment's own
+// full blocks (id < nfull) or one of this CTA's scratch blocks (nfull ..
+// nfull + IP_S - 1).  Before the first round the map is the identity and the
+// segment's partial last block lies in place (IP_TAIL).  A round (Alg. 5 on
+// one processor, with the output on the block grid of the grid layout) reads
+// the sequence tile by tile; a tile's blocks go to the free list once it is
+// in shared memory; the tile is ranked stably by the round's digit; every
+// output block that the tile is the first to touch takes the next free block;
+// then the tile is stored.  After the last round, Finalize (Alg. 7) moves
+// logical block j to place j along chains, which start at a place that holds
+// no block (a free one, or the segment's tail), and along cycles, which are
+// first cut into chains through free scratch blocks.
+//
+// Free blocks suffice: after a tile the output touches at most (elements
+// stored) / IP_B + 2 sigma blocks (each bucket's run adds at most a partial
+// block at each end), the unread input holds at most the rest of the
+// segment's blocks, and the CTA owns nfull + IP_S blocks, IP_S = 2 sigma + 2.
+// A segment no longer than the scratch is sorted out of place between the
+// two instead (the paper's switch for arrays up to the size of T, Sec. 5).
+constexpr uint32_t IP_LB = 5;
+constexpr uint32_t IP_B = 1u << IP_LB;
+constexpr uint32_t IP_NB = SEG_MED >> IP_LB; // blocks of the longest medium segment
+constexpr uint32_t IP_S = 2 * 256 + 2;       // scratch blocks per CTA (8-bit digits)
+constexpr uint32_t IP_FCAP = IP_NB + IP_S;   // free list: every block at most once
+constexpr uint16_t IP_NONE = 0xFFFF, IP_CLAIM = 0xFFFE, IP_TAIL = 0xFFFD;
+constexpr int IP_K = 16;                     // block moves per warp step in Finalize
+constexpr uint32_t IP_CUT = 16;              // a cycle is cut into chains of at most this many moves
+
+template <typename KT, bool HASV, int TILE> struct IpCfg {
+    static constexpr int SIGMA = 256;
+    static constexpr int NTD = int(sizeof(KT)) * 8 / 8;
+    using TP = TilePass<KT, HASV, 8, TILE / (32 * SEG_NW)>;
+    static constexpr size_t O_TV = size_t(TILE) * sizeof(KT);
+    static constexpr size_t O_CNT = O_TV + (HASV ? size_t(TILE) * 4 : 0);
+    static constexpr size_t O_GH = O_CNT + size_t(3) * SIGMA * 4; // tcnt, bstart, run
+    static constexpr size_t O_MAP = O_GH + size_t(NTD) * SIGMA * 4;
+    static constexpr size_t O_RING = O_MAP + size_t(2) * IP_NB * 2;
+    static constexpr size_t O_SCR = (O_RING + size_t(IP_FCAP) * 2 + 15) / 16 * 16;
+    static constexpr size_t SMEM = O_SCR + TP::SCRATCH;
+    // Finalize reuses the tile buffer: the free scratch blocks and the cut list
+    static_assert(size_t(TILE) * sizeof(KT) >= 1600 + IP_NB, "tile buffer holds the Finalize lists");
+    static_assert(TP::SCRATCH >= size_t(SEG_NW) * 2 * IP_K * 4, "scratch holds the move lists");
+};
+
+template <typename KT, bool HASV, int TILE>
+__global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
+{
+    using C = IpCfg<KT, HASV, TILE>;
+    constexpr int SIGMA = C::SIGMA, DB = 8, LIT = TILE / SEG_T;
+    constexpr uint32_t IP_HELD = 0xFFFFFFFFu, IP_TAILDST = 0xFFFFFFFEu;
+    extern __shared__ __align__(16) unsigned char sm[];
+    KT *tk = reinterpret_cast<KT *>(sm);
+    uint32_t *tv = reinterpret_cast<uint32_t *>(sm + C::O_TV);
+    uint32_t *tcnt = reinterpret_cast<uint32_t *>(sm + C::O_CNT);
+    uint32_t *bstart = tcnt + SIGMA;
+    uint32_t *run = bstart + SIGMA;
+    uint32_t *gh = reinterpret_cast<uint32_t *>(sm + C::O_GH);
+    uint16_t *mapA = reinterpret_cast<uint16_t *>(sm + C::O_MAP);
+    uint16_t *mapB = mapA + IP_NB;
+    uint16_t *ring = reinterpret_cast<uint16_t *>(sm + C::O_RING);
+    unsigned char *scratch = sm + C::O_SCR;
+    __shared__ uint32_t s_t, s_fh, s_ft, s_next, s_next2, s_nfree, s_fuse, s_nfl, s_fl2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    KT *keys = static_cast<KT *>(a.keys);
+    KT *Tk = static_cast<KT *>(a.scr_k) + size_t(blockIdx.x) * (IP_S * IP_B);
+    uint32_t *Tv = HASV ? a.scr_v + size_t(blockIdx.x) * (IP_S * IP_B) : nullptr;
+    const uint32_t count = a.ctr[1];
+    for (;;) {
+        __syncthreads(); // every thread has read s_t and finished the last segment
+        if (tid == 0)
+            s_t = atomicAdd(&a.ctr[3], 1u);
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t >= count)
+            break;
+        const uint32_t sgi = a.med_list[t];
+        const unsigned long long o = a.off[sgi];
+        const unsigned long long len = a.off[sgi + 1] - o;
+        if (len > SEG_MED) { // the classifier lists no such segment
+            if (tid == 0)
+                set_status(ST_INTERNAL);
+            continue;
+        }
+        const uint32_t m = static_cast<uint32_t>(len);
+        KT *Ak = keys + o;
+        uint32_t *Av = HASV ? a.vals + o : nullptr;
+        const uint32_t nfull = m >> IP_LB, part = m & (IP_B - 1), nb = nfull + (part ? 1u : 0u);
+        const uint32_t nphys = nfull + IP_S;
+        // the block of physical id ph < nphys (the partial block in place is
+        // only ever read, in the first round, straight from the segment)
+        auto koff = [&](uint32_t ph) -> KT * {
+            return ph < nfull ? Ak + (size_t(ph) << IP_LB) : Tk + (size_t(ph - nfull) << IP_LB);
+        };
+        auto voff = [&](uint32_t ph) -> uint32_t * {
+            return ph < nfull ? Av + (size_t(ph) << IP_LB) : Tv + (size_t(ph - nfull) << IP_LB);
+        };
+        uint16_t *pi = mapA, *pin = mapB;
+        // setup (Alg. 4): the segment's blocks in order, the partial one in
+        // place; the free list holds the scratch blocks
+        for (uint32_t q = tid; q < nb; q += SEG_T)
+            pi[q] = q < nfull ? static_cast<uint16_t>(q) : IP_TAIL;
+        for (uint32_t k = tid; k < IP_S; k += SEG_T)
+            ring[k] = static_cast<uint16_t>(nfull + k);
+        for (int i = tid; i < C::NTD * SIGMA; i += SEG_T)
+            gh[i] = 0;
+        if (tid == 0) {
+            s_fh = 0;
+            s_ft = IP_S;
+        }
+        __syncthreads();
+        // every digit's counts in one pass: the multiset is the same in every round
+        for (uint32_t i = tid; i < m; i += SEG_T) {
+            const KT k = Ak[i];
+#pragma unroll
+            for (int r = 0; r < C::NTD; ++r)
+                atomicAdd(&gh[r * SIGMA + digit_of(k, uint32_t(r * DB), SIGMA - 1)], 1u);
+        }
+        __syncthreads();
+        auto starts = [&](int r) { // bucket starts: exclusive prefix of round r's counts (warp 0)
+            if (warp == 0) {
+                uint32_t carry = 0;
+                for (int c0 = 0; c0 < SIGMA; c0 += 32) {
+                    const uint32_t v = gh[r * SIGMA + c0 + lane];
+                    const uint32_t inc = warp_incl_scan(v);
+                    run[c0 + lane] = carry + inc - v;
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                }
+            }
+        };
+        if (m <= IP_S * IP_B) {
+            // no longer than the scratch: out of place between the segment
+            // and the scratch, which serves as A' of Alg. 1
+            KT *sk = Ak, *dk = Tk;
+            uint32_t *sv = Av, *dv = Tv;
+            for (int r = 0; r < C::NTD; ++r) {
+                const uint32_t shift = uint32_t(r * DB);
+                starts(r);
+                for (uint32_t t0 = 0; t0 < m; t0 += TILE) {
+                    const uint32_t cnt = min(uint32_t(TILE), m - t0);
+#pragma unroll
+                    for (int it = 0; it < LIT; ++it) {
+                        const uint32_t i = it * SEG_T + tid;
+                        if (i < cnt) {
+                            tk[i] = sk[t0 + i];
+                            if (HASV)
+                                tv[i] = sv[t0 + i];
+                        }
+                    }
+                    __syncthreads();
+                    C::TP::run(tk, tv, tk, tv, cnt, shift, scratch, tcnt, bstart);
+#pragma unroll
+                    for (int it = 0; it < LIT; ++it) {
+                        const uint32_t i = it * SEG_T + tid;
+                        if (i >= cnt)
+                            continue;
+                        const KT k = tk[i];
+                        const uint32_t d = digit_of(k, shift, SIGMA - 1);
+                        const uint32_t pos = run[d] + (i - bstart[d]);
+                        if (pos >= m) { // only inconsistent counts get here
+                            set_status(ST_INTERNAL);
+                            continue;
+                        }
+                        dk[pos] = k;
+                        if (HASV)
+                            dv[pos] = tv[i];
+                    }
+                    __syncthreads();
+                    for (int c = tid; c < SIGMA; c += SEG_T)
+                        run[c] += tcnt[c];
+                    __syncthreads();
+                }
+                KT *xk = sk;
+                sk = dk;
+                dk = xk;
+                uint32_t *xv = sv;
+                sv = dv;
+                dv = xv;
+            }
+            if (sk != Ak) // an odd number of rounds: the result is in the scratch
+                for (uint32_t i = tid; i < m; i += SEG_T) {
+                    Ak[i] = sk[i];
+                    if (HASV)
+                        Av[i] = sv[i];
+                }
+            continue;
+        }
+        for (int r = 0; r < C::NTD; ++r) {
+            const uint32_t shift = uint32_t(r * DB);
+            starts(r);
+            for (uint32_t j = tid; j < nb; j += SEG_T)
+                pin[j] = IP_NONE;
+            __syncthreads();
+            for (uint32_t t0 = 0; t0 < m; t0 += TILE) {
+                const uint32_t cnt = min(uint32_t(TILE), m - t0);
+                const uint32_t ft = s_ft;
+                // the tile, read through the block map (the first round's map
+                // is the identity: the segment in place)
+                if (r == 0) {
+#pragma unroll
+                    for (int it = 0; it < LIT; ++it) {
+                        const uint32_t i = it * SEG_T + tid;
+                        if (i < cnt) {
+                            tk[i] = Ak[t0 + i];
+                            if (HASV)
+                                tv[i] = Av[t0 + i];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int it = 0; it < LIT; ++it) {
+                        const uint32_t i = it * SEG_T + tid;
+                        if (i < cnt) {
+                            const uint32_t e = t0 + i, ph = pi[e >> IP_LB], w = e & (IP_B - 1);
+                            const bool ok = ph < nphys; // else a broken map, reported
+                            if (!ok)
+                                set_status(ST_INTERNAL);
+                            tk[i] = ok ? koff(ph)[w] : KT(0);
+                            if (HASV)
+                                tv[i] = ok ? voff(ph)[w] : 0u;
+                        }
+                    }
+                }
+                // its blocks are free now (the partial block in place is never
+                // reused: it is shorter than a block)
+                const uint32_t q0 = t0 >> IP_LB, nq = ((t0 + cnt - 1) >> IP_LB) - q0 + 1;
+                const uint32_t npush = nq - (pi[q0 + nq - 1] == IP_TAIL ? 1u : 0u);
+                for (uint32_t k = tid; k < npush; k += SEG_T)
+                    ring[(ft + k) % IP_FCAP] = pi[q0 + k];
+                const uint32_t fend = ft + npush;
+                __syncthreads();
+                if (tid == 0)
+                    s_ft = fend;
+                C::TP::run(tk, tv, tk, tv, cnt, shift, scratch, tcnt, bstart);
+                // each output block this tile touches first takes a free block
+                auto take = [&](uint32_t k) -> uint16_t {
+                    if (k >= fend) { // more blocks than the bound allows
+                        set_status(ST_INTERNAL);
+                        return IP_NONE;
+                    }
+                    return ring[k % IP_FCAP];
+                };
+                auto claim = [&](uint32_t j) {
+                    return pin[j] == IP_NONE && atomicCAS(&pin[j], IP_NONE, IP_CLAIM) == IP_NONE;
+                };
+                for (int c = tid; c < SIGMA; c += SEG_T) { // whole warps: SIGMA % SEG_T == 0
+                    const uint32_t cn = tcnt[c];
+                    uint32_t j0 = 0, j1 = 0, need = 0;
+                    bool w0 = false, w1 = false;
+                    if (cn) {
+                        const uint32_t g = run[c];
+                        j0 = g >> IP_LB;
+                        j1 = (g + cn - 1) >> IP_LB;
+                        if (j1 >= nb) {
+                            set_status(ST_INTERNAL);
+                        } else {
+                            // the run's end blocks may be shared with the
+                            // neighbouring buckets; blocks inside it are its own
+                            w0 = claim(j0);
+                            w1 = j1 != j0 && claim(j1);
+                            need = (w0 ? 1u : 0u) + (w1 ? 1u : 0u) + (j1 > j0 + 1 ? j1 - j0 - 1 : 0u);
+                        }
+                    }
+                    // one free-list reservation per warp
+                    const uint32_t incl = warp_incl_scan(need), tot = __shfl_sync(0xffffffffu, incl, 31);
+                    uint32_t k = 0;
+                    if (lane == 31 && tot)
+                        k = atomicAdd(&s_fh, tot);
+                    k = __shfl_sync(0xffffffffu, k, 31) + incl - need;
+                    if (need) {
+                        if (w0)
+                            pin[j0] = take(k++);
+                        for (uint32_t j = j0 + 1; j < j1; ++j)
+                            pin[j] = take(k++);
+                        if (w1)
+                            pin[j1] = take(k++);
+                    }
+                }
+                __syncthreads();
+                // stores: a bucket's elements are consecutive in the tile and in the output
+#pragma unroll
+                for (int it = 0; it < LIT; ++it) {
+                    const uint32_t i = it * SEG_T + tid;
+                    if (i >= cnt)
+                        continue;
+                    const KT k = tk[i];
+                    const uint32_t d = digit_of(k, shift, SIGMA - 1);
+                    const uint32_t pos = run[d] + (i - bstart[d]);
+                    const uint32_t ph = (pos >> IP_LB) < nb ? pin[pos >> IP_LB] : IP_NONE;
+                    if (ph >= nphys) {
+                        set_status(ST_INTERNAL);
+                        continue;
+                    }
+                    koff(ph)[pos & (IP_B - 1)] = k;
+                    if (HASV)
+                        voff(ph)[pos & (IP_B - 1)] = tv[i];
+                }
+                __syncthreads();
+                for (int c = tid; c < SIGMA; c += SEG_T)
+                    run[c] += tcnt[c];
+                __syncthreads();
+            }
+            uint16_t *x = pi;
+            pi = pin;
+            pin = x;
+        }
+        // Finalize (Alg. 7): logical block j to place j, the partial one to
+        // the segment's tail.  occ[p]: the logical block in place p's block.
+        // The tile buffer holds the free scratch blocks, their use flags and
+        // the cycles left uncut.
+        uint16_t *occ = pin;
+        uint16_t *freeT = reinterpret_cast<uint16_t *>(sm);
+        unsigned char *usedT = sm + 1040;
+        uint16_t *flist = reinterpret_cast<uint16_t *>(sm + 1600);
+        for (uint32_t p = tid; p < nb; p += SEG_T)
+            occ[p] = IP_NONE;
+        for (uint32_t k = tid; k < IP_S; k += SEG_T)
+            usedT[k] = 0;
+        if (tid == 0)
+            s_next = s_next2 = s_nfree = s_fuse = s_nfl = s_fl2 = 0;
+        __syncthreads();
+        for (uint32_t j = tid; j < nb; j += SEG_T) {
+            const uint32_t ph = pi[j];
+            if (ph < nfull)
+                occ[ph] = static_cast<uint16_t>(j);
+            else if (ph < nphys)
+                usedT[ph - nfull] = 1;
+        }
+        __syncthreads();
+        for (uint32_t k = tid; k < IP_S; k += SEG_T)
+            if (!usedT[k])
+                freeT[atomicAdd(&s_nfree, 1u)] = static_cast<uint16_t>(nfull + k);
+        __syncthreads();
+        const uint32_t nfree = s_nfree;
+        // a warp moves blocks IP_K at a time: every source into registers,
+        // then every destination.  mv: this warp's list of (destination,
+        // source block); IP_HELD names a cycle's first block, held in hk/hv
+        uint32_t *mv = reinterpret_cast<uint32_t *>(scratch) + warp * (2 * IP_K);
+        auto step = [&](int n, KT hk, uint32_t hv) {
+            __syncwarp();
+            KT rk[IP_K];
+            uint32_t rv[IP_K];
+#pragma unroll
+            for (int i = 0; i < IP_K; ++i) {
+                rk[i] = hk;
+                rv[i] = hv;
+                const uint32_t src = i < n ? mv[2 * i + 1] : IP_HELD;
+                if (src < nphys) {
+                    rk[i] = koff(src)[lane];
+                    if (HASV)
+                        rv[i] = voff(src)[lane];
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < IP_K; ++i) {
+                if (i >= n)
+                    continue;
+                const uint32_t dst = mv[2 * i], src = mv[2 * i + 1];
+                if ((src >= nphys && src != IP_HELD) || (dst >= nphys && dst != IP_TAILDST)) {
+                    if (lane == 0)
+                        set_status(ST_INTERNAL); // a broken map
+                    continue;
+                }
+                const bool tail = dst == IP_TAILDST;
+                const uint32_t lim = tail ? part : IP_B;
+                if (uint32_t(lane) < lim) {
+                    (tail ? Ak + (size_t(nfull) << IP_LB) : koff(dst))[lane] = rk[i];
+                    if (HASV)
+                        (tail ? Av + (size_t(nfull) << IP_LB) : voff(dst))[lane] = rv[i];
+                }
+            }
+            __syncwarp();
+        };
+        // cycles: the least place of each cycle leads it; the leader's warp
+        // copies every IP_CUT-th block of the cycle to a free scratch block,
+        // which leaves that place empty, so the cycle falls into chains of at
+        // most IP_CUT moves.  Without free scratch blocks left, a cycle is
+        // moved whole after the chains.
+        for (;;) {
+            uint32_t b0 = 0;
+            if (lane == 0)
+                b0 = atomicAdd(&s_next, 32u);
+            const uint32_t base = __shfl_sync(0xffffffffu, b0, 0);
+            if (base >= nfull)
+                break;
+            const uint32_t p = base + lane;
+            bool lead = false;
+            if (p < nfull) {
+                uint32_t x = pi[p];
+                if (x < nfull && x != p) {
+                    for (uint32_t g = 0; g <= nb; ++g) {
+                        if (x >= nfull || x < p) // a chain, or not the least place of its cycle
+                            break;
+                        if (x == p) {
+                            lead = true;
+                            break;
+                        }
+                        x = pi[x];
+                    }
+                }
+            }
+            unsigned lm = __ballot_sync(0xffffffffu, lead);
+            while (lm) {
+                const int l = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const uint32_t d0 = base + l;
+                uint32_t L = 1;
+                for (uint32_t x = pi[d0]; x != d0 && x < nfull && L <= nb; x = pi[x])
+                    ++L;
+                const uint32_t ncut = (L + IP_CUT - 1) / IP_CUT;
+                uint32_t k = 0;
+                if (lane == 0)
+                    k = atomicAdd(&s_fuse, ncut);
+                k = __shfl_sync(0xffffffffu, k, 0);
+                if (k + ncut > nfree) {
+                    if (lane == 0)
+                        flist[atomicAdd(&s_nfl, 1u)] = static_cast<uint16_t>(d0);
+                    continue;
+                }
+                uint32_t x = d0;
+                int n = 0;
+                for (uint32_t i = 0; i < L; ++i) {
+                    if (i % IP_CUT == 0) {
+                        if (lane == 0) {
+                            mv[2 * n] = freeT[k];
+                            mv[2 * n + 1] = x;
+                        }
+                        ++k;
+                        ++n;
+                    }
+                    const bool last = i + 1 == L;
+                    if (n == IP_K || (last && n)) {
+                        step(n, KT(0), 0u);
+                        // the cut places hold nothing now; their blocks'
+                        // logical owners point at the copies
+                        if (lane == 0)
+                            for (int q = 0; q < n; ++q) {
+                                const uint32_t cx = mv[2 * q + 1];
+                                pi[occ[cx]] = static_cast<uint16_t>(mv[2 * q]);
+                                occ[cx] = IP_NONE;
+                            }
+                        __syncwarp();
+                        n = 0;
+                    }
+                    if (!last)
+                        x = pi[x];
+                }
+            }
+        }
+        __syncthreads();
+        // chains: every place that holds no block starts one (a free place,
+        // or the tail); each step takes up to IP_K moves, the next chain
+        // where one ends.  A move reads a place that the chain's previous
+        // move writes only in a later step, or later in the same step.
+        {
+            uint32_t base = 0, cur = 0, moves = 0;
+            unsigned smask = 0;
+            auto next_start = [&]() -> bool { // warp-uniform
+                while (!smask) {
+                    uint32_t b0 = 0;
+                    if (lane == 0)
+                        b0 = atomicAdd(&s_next2, 32u);
+                    base = __shfl_sync(0xffffffffu, b0, 0);
+                    if (base >= nb)
+                        return false;
+                    const uint32_t p = base + lane;
+                    smask = __ballot_sync(0xffffffffu, p < nb && (p == nfull || occ[p] == IP_NONE));
+                }
+                const int l = __ffs(smask) - 1;
+                smask &= smask - 1;
+                cur = base + l;
+                return true;
+            };
+            bool have = next_start();
+            while (have) {
+                int n = 0;
+                while (have && n < IP_K) {
+                    const uint32_t src = pi[cur];
+                    if (lane == 0) {
+                        mv[2 * n] = cur == nfull ? IP_TAILDST : cur;
+                        mv[2 * n + 1] = src;
+                    }
+                    ++n;
+                    if (++moves > nb) { // only a broken map walks this far
+                        if (lane == 0)
+                            set_status(ST_INTERNAL);
+                        have = false;
+                    } else if (src >= nfull) { // a scratch block: the chain ends
+                        have = next_start();
+                    } else {
+                        cur = src;
+                    }
+                }
+                step(n, KT(0), 0u);
+            }
+        }
+        __syncthreads();
+        // cycles left whole: the first place's block waits in registers
+        // until the cycle closes
+        const uint32_t nfl = s_nfl;
+        for (;;) {
+            uint32_t f = 0;
+            if (lane == 0)
+                f = atomicAdd(&s_fl2, 1u);
+            f = __shfl_sync(0xffffffffu, f, 0);
+            if (f >= nfl)
+                break;
+            const uint32_t d0 = flist[f];
+            const KT hk = Ak[(size_t(d0) << IP_LB) + lane];
+            const uint32_t hv = HASV ? Av[(size_t(d0) << IP_LB) + lane] : 0u;
+            uint32_t cur = d0, moves = 0;
+            bool end = false;
+            while (!end) {
+                int n = 0;
+                while (!end && n < IP_K) {
+                    uint32_t src = pi[cur];
+                    if (src == d0 || ++moves > nb || src >= nfull) {
+                        if (src != d0 && lane == 0)
+                            set_status(ST_INTERNAL); // a cycle runs through no scratch block
+                        src = IP_HELD;
+                        end = true;
+                    }
+                    if (lane == 0) {
+                        mv[2 * n] = cur;
+                        mv[2 * n + 1] = src;
+                    }
+                    ++n;
+                    cur = src;
+                }
+                step(n, hk, hv);
+            }
+        }
+    }
+}
+
 } // namespace
 
 // ---------------------------------------------------------------- host side
@@ -322,6 +864,10 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
         return 2 * TILE * sizeof(KT) + (HASV ? 2 * TILE * 4 : 0) + 2 * SIGMA * 4 + SIGMA * 8 +
                SIGMA * 4 + TPm::SCRATCH;
     }
+    // the in-place medium pass (8-bit digits): 4096-element tiles for 4-byte
+    // keys, 2048 for 8-byte ones, so that two CTAs fit on an SM
+    static constexpr int IP_TILE = sizeof(KT) == 4 ? 4096 : 2048;
+    using IC = IpCfg<KT, HASV, IP_TILE>;
     static cudaError_t launch(const SegArgs &a, cudaStream_t st, int med_ctas)
     {
         static DeviceOnce attr;
@@ -331,6 +877,10 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_seg_medium<KT, HASV, DB, TILE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(med_smem()));
+            if constexpr (DB == 8)
+                if (e == cudaSuccess)
+                    e = cudaFuncSetAttribute(k_seg_medium_ip<KT, HASV, IP_TILE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(IC::SMEM));
             return e;
         });
         if (ea != cudaSuccess)
@@ -340,8 +890,14 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
                                                       small_smem());
         const int sms = num_sms();
         k_seg_small<KT, HASV, DB, SMALL><<<sms * (per > 0 ? per : 1), SEG_T, small_smem(), st>>>(a);
-        if (a.med_stride)
+        if (a.med_ip) {
+            if constexpr (DB == 8)
+                k_seg_medium_ip<KT, HASV, IP_TILE><<<med_ctas, SEG_T, IC::SMEM, st>>>(a);
+            else
+                return cudaErrorInvalidValue; // the planner picks it for 8-bit digits only
+        } else if (a.med_stride) {
             k_seg_medium<KT, HASV, DB, TILE><<<med_ctas, SEG_T, med_smem(), st>>>(a);
+        }
         g_launches += 2;
         return cudaGetLastError();
     }
@@ -363,19 +919,29 @@ uint32_t seg_med_ctas(uint32_t med_max, int kb, bool hasv, size_t budget)
     return c < most ? static_cast<uint32_t>(c) : most;
 }
 
-// med_max: the longest medium segment (0: none), the per-CTA scratch stride
-size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg, uint32_t med_max, uint32_t med_ctas)
+// CTAs of the in-place medium pass: two per SM
+uint32_t seg_ip_ctas() { return static_cast<uint32_t>(num_sms()) * 2; }
+
+// elements of scratch per CTA of the medium pass: its scratch blocks in
+// place (ip), else an out-of-place buffer as long as the longest medium
+// segment (med_max, 0: none)
+static size_t seg_med_stride(bool ip, uint32_t med_max) { return !med_max ? 0 : ip ? size_t(IP_S) * IP_B : med_max; }
+
+size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg, uint32_t med_max, uint32_t med_ctas, bool ip)
 {
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
-    return up(64) + 2 * up(nseg * 4) + up(size_t(med_ctas) * med_max * kb) +
-           (hasv ? up(size_t(med_ctas) * med_max * 4) : 0);
+    const size_t per = seg_med_stride(ip, med_max);
+    return up(64) + 2 * up(nseg * 4) + up(size_t(med_ctas) * per * kb) +
+           (hasv ? up(size_t(med_ctas) * per * 4) : 0);
 }
 
 cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long long *off_dev,
-                             size_t nseg, int kb, int db, uint32_t med_max, uint32_t med_ctas, void *scratch,
-                             cudaStream_t st)
+                             size_t nseg, int kb, int db, uint32_t med_max, uint32_t med_ctas, bool ip,
+                             void *scratch, cudaStream_t st)
 {
+    if (ip && db != 8)
+        return cudaErrorInvalidValue;
     const size_t al = 256;
     auto up = [&](size_t x) { return (x + al - 1) / al * al; };
     char *p = static_cast<char *>(scratch);
@@ -390,10 +956,12 @@ cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long lon
     p += up(nseg * 4);
     a.med_list = reinterpret_cast<uint32_t *>(p);
     p += up(nseg * 4);
+    const size_t per = seg_med_stride(ip, med_max);
     a.scr_k = p;
-    p += up(size_t(med_ctas) * med_max * kb);
+    p += up(size_t(med_ctas) * per * kb);
     a.scr_v = vals ? reinterpret_cast<uint32_t *>(p) : nullptr;
     a.med_stride = med_max;
+    a.med_ip = ip && med_max ? 1u : 0u;
     a.nt = (8 * kb + db - 1) / db;
     a.db = db;
     cudaError_t e = cudaMemsetAsync(a.ctr, 0, 64, st);

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
             "radsort_sort": ([vp, vp, sz, i, i, vp], i),
             "radsort_sort_noalloc": ([vp, vp, sz, i, i, vp], i),
             "radsort_segmented_workspace_size": ([vp, sz, i, i, i, ctypes.POINTER(sz)], i),
+            "radsort_segmented_workspace_size_min": ([vp, sz, i, i, i, ctypes.POINTER(sz)], i),
             "radsort_sort_segmented": ([vp, vp, vp, vp, sz, i, i, vp, sz, vp], i),
             "radsort_lsd_oop_segmented_workspace_size": ([vp, sz, i, i, i, ctypes.POINTER(sz)], i),
             "radsort_lsd_oop_sort_segmented": ([vp, vp, vp, vp, vp, vp, sz, i, i, vp, sz, vp], i),
@@ -102,7 +103,8 @@ def lib() -> ctypes.CDLL:
 # exported names declared in include/radsort.h
 EXPORTS = ("radsort_status_str", "radsort_plan_default", "radsort_autotune", "radsort_autotune_digits",
            "radsort_segmented_autotune", "radsort_workspace_size", "radsort_sort",
-           "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_sort_segmented",
+           "radsort_sort_noalloc", "radsort_segmented_workspace_size", "radsort_segmented_workspace_size_min",
+           "radsort_sort_segmented",
            "radsort_lsd_oop_segmented_workspace_size", "radsort_lsd_oop_sort_segmented",
            "radsort_sort_ex", "radsort_sort_rounds", "radsort_lsd_oop_sort",
            "radsort_lsd_oop_scratch_size", "radsort_float_keys",
@@ -299,14 +301,16 @@ def lsd_oop_tensors(keys, values, keys_alt, values_alt, *, digit_bits=8, stream=
                          _key_bytes(keys), digit_bits, _torch_stream(stream))
 
 
-def segmented_workspace_size(offsets_host, key_bytes, value_bytes, digit_bits=8):
-    """offsets_host: numpy uint64 array of num_segments + 1 offsets."""
+def segmented_workspace_size(offsets_host, key_bytes, value_bytes, digit_bits=8, *, minimal=False):
+    """offsets_host: numpy uint64 array of num_segments + 1 offsets.  minimal:
+    the smallest workspace the sort accepts (the low-memory plan: medium
+    segments sorted in place, 8-bit digits), else the fast plan's."""
     import numpy as np
     oh = np.ascontiguousarray(offsets_host, dtype=np.uint64)
     out = ctypes.c_size_t(0)
-    _ok(lib().radsort_segmented_workspace_size(oh.ctypes.data_as(ctypes.c_void_p), oh.size - 1,
-                                               key_bytes, value_bytes, digit_bits, ctypes.byref(out)),
-        "radsort_segmented_workspace_size")
+    name = "radsort_segmented_workspace_size_min" if minimal else "radsort_segmented_workspace_size"
+    _ok(getattr(lib(), name)(oh.ctypes.data_as(ctypes.c_void_p), oh.size - 1,
+                             key_bytes, value_bytes, digit_bits, ctypes.byref(out)), name)
     return int(out.value)
 
 

@@ -157,10 +157,10 @@ def test_segmented_workspace_size(lib):
 
     from paper_2607_05302_gb300 import radsort as R
 
-    def ws(lens):
+    def ws(lens, db=8):
         off = np.zeros(len(lens) + 1, np.uint64)
         np.cumsum(np.array(lens, np.uint64), out=off[1:])
-        return R.segmented_workspace_size(off, 4, 4, 8)
+        return R.segmented_workspace_size(off, 4, 4, db)
 
     with pytest.raises(R.RadsortError):
         R.segmented_workspace_size(np.array([0, 10, 5], np.uint64), 4, 4, 8)
@@ -184,6 +184,23 @@ def test_segmented_workspace_size(lib):
         return R.lsd_oop_segmented_workspace_size(off, 4, 4, 8)
 
     assert ows([big]) - ows([100]) < one                             # no block store, only scratch
+
+    # the smallest workspace accepted: the low-memory plan (8-bit digits,
+    # medium segments in place, a fixed 514 blocks of 32 elements per CTA,
+    # 2 CTAs per SM; no device here: 152 SMs) where it is the smaller
+    def mws(lens, db=8):
+        off = np.zeros(len(lens) + 1, np.uint64)
+        np.cumsum(np.array(lens, np.uint64), out=off[1:])
+        return R.segmented_workspace_size(off, 4, 4, db, minimal=True)
+
+    in_place = 2 * 152 * 514 * 32 * 8
+    many = [1 << 18] * 2000
+    assert abs(mws(many) - ws([100] * 2000) - in_place) <= 1024
+    assert mws(many) < ws(many) / 5                                 # the fast plan holds 6% of the arrays
+    for lens in ([1 << 18] * 20, mixed, [5000]):                    # never above the fast plan's
+        assert mws(lens) <= ws(lens)
+    assert abs(mws([1 << 18] * 20) - ws([100] * 20) - 20 * 514 * 32 * 8) <= 1024  # no more CTAs than segments
+    assert mws(mixed, 11) == ws(mixed, 11)                          # 11-bit digits: one plan
 
 
 def test_binding_signatures_match_the_header(lib):

@@ -19,7 +19,7 @@ def offsets_of(lengths):
     return off
 
 
-def run_segmented(keys_np, lengths, digit_bits=8, caller_ws=True):
+def run_segmented(keys_np, lengths, digit_bits=8, caller_ws=True, minimal=False):
     off = offsets_of(lengths)
     n = int(off[-1])
     kt = torch.from_numpy(keys_np.view(np.int32 if keys_np.dtype == np.uint32 else np.int64)).to(DEV)
@@ -27,7 +27,7 @@ def run_segmented(keys_np, lengths, digit_bits=8, caller_ws=True):
     od = torch.from_numpy(off.view(np.int64)).to(DEV)
     ws = None
     if caller_ws:
-        need = R.segmented_workspace_size(off, keys_np.itemsize, 4, digit_bits)
+        need = R.segmented_workspace_size(off, keys_np.itemsize, 4, digit_bits, minimal=minimal)
         ws = torch.empty(max(need, 1), dtype=torch.uint8, device=DEV)
     R.sort_segmented_tensors(kt, vt, od, off, digit_bits=digit_bits, workspace=ws)
     R.radsort_device_status()
@@ -66,6 +66,62 @@ def test_segmented_u32_vs_oracle(lengths, digit_bits):
     ek, ev = oracle_segmented_u32(keys, lens, digit_bits)
     assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
     assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
+# medium lengths on and off the 32-element block grid, on both sides of the
+# in-place threshold (16448 = 514 blocks of 32), and two short ones
+MEDIUM_SET = [4097, 4128, 8192, 16448, 16449, 20000, 65536, 65537, 100000, 131071, 262143, 262144, 33, 4099]
+
+
+@pytest.mark.parametrize("dist", ["uniform", "equal", "sorted", "reverse", "zipf", "few"])
+def test_low_memory_plan_medium_segments_vs_oracle(dist):
+    """The low-memory plan (a caller workspace of the minimal size): medium
+    segments sorted in place by one CTA each, several per CTA, with key
+    distributions that give the block maps different shapes (one bucket per
+    round, runs in input order or reversed, a few heavy buckets, three
+    distinct keys); bit-exact against the oracle's stable sort of each
+    segment."""
+    lens = MEDIUM_SET * 3
+    off = offsets_of(lens)
+    assert R.segmented_workspace_size(off, 4, 4, 8, minimal=True) < R.segmented_workspace_size(off, 4, 4, 8)
+    n = sum(lens)
+    if dist == "few":
+        keys = (W.make_keys("uniform", n) % np.uint32(3)) * np.uint32(0x01010101)
+    else:
+        keys = W.make_keys(dist, n)
+    kt, vt, _ = run_segmented(keys, lens, 8, minimal=True)
+    ek, ev = oracle_segmented_u32(keys, lens, 8)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
+def test_low_memory_plan_mixed_and_u64_keys_only():
+    """The low-memory plan beside long and short segments, and with 8-byte
+    keys and no values."""
+    lens = [int(x) for x in LENGTH_SETS["mixed"]] + [40000, 200000]
+    n = sum(lens)
+    keys = W.make_keys("uniform", n)
+    kt, vt, _ = run_segmented(keys, lens, 8, minimal=True)
+    ek, ev = oracle_segmented_u32(keys, lens, 8)
+    assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+    lens = [4097, 70001, 262144, 5000, 131072, 17000]
+    n = sum(lens)
+    keys = W.make_keys("uniform", n, 64)
+    keys[::7] = keys[5]  # ties
+    off = offsets_of(lens)
+    need = R.segmented_workspace_size(off, 8, 0, 8, minimal=True)
+    assert need < R.segmented_workspace_size(off, 8, 0, 8)
+    kt = torch.from_numpy(keys.view(np.int64)).to(DEV)
+    od = torch.from_numpy(off.view(np.int64)).to(DEV)
+    ws = torch.empty(need, dtype=torch.uint8, device=DEV)
+    R.sort_segmented_tensors(kt, None, od, off, digit_bits=8, workspace=ws)
+    R.radsort_device_status()
+    got = kt.cpu().numpy().view(np.uint64)
+    for s_ in range(len(lens)):
+        a, b = int(off[s_]), int(off[s_ + 1])
+        ek, _ = oracle.lsd_oop(keys[a:b], np.arange(b - a, dtype=np.uint32), n_t=8, sigma=256, bits=8)
+        assert np.array_equal(got[a:b], ek)
 
 
 @pytest.mark.parametrize("digit_bits", [8, 11])
