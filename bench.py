@@ -354,7 +354,8 @@ def run_segmented(a):
     timed replay sorts a fresh copy (restored outside the timed region).
     Beside it, the out-of-place comparator on the same arrays
     (radsort_lsd_oop_sort_segmented: the long segments through n-element
-    alternate arrays), captured and timed the same way."""
+    alternate arrays), and the sort given the smallest workspace it accepts
+    (the low-memory plan), captured and timed the same way."""
     import numpy as np
     import torch
 
@@ -413,6 +414,14 @@ def run_segmented(a):
         ms, ok = timed(lambda kt, vt: R.sort_segmented_tensors(kt, vt, od, off, digit_bits=db, workspace=ws))
         res[db] = {"ms_per_step": ms, "value": n / (ms / 1e3) / 1e9, "workspace_bytes": need, "checked": ok}
         del ws
+    # the smallest workspace the sort accepts (8-bit digits): medium segments
+    # and unaligned long ones sorted in place
+    need_m = R.segmented_workspace_size(off, 4, 4, 8, minimal=True)
+    wsm = torch.empty(need_m, dtype=torch.uint8, device=dev)
+    mms, mok = timed(lambda kt, vt: R.sort_segmented_tensors(kt, vt, od, off, digit_bits=8, workspace=wsm))
+    low = {"value": round(n / (mms / 1e3) / 1e9, 3), "ms_per_step": round(mms, 3), "checked": mok,
+           "extra_bytes": need_m, "extra_frac": round(need_m / (n * 8), 4), "digit_bits": 8}
+    del wsm
     # the digit width the library's autotuner picks for this batch
     best = R.segmented_autotune(keys0, vals0, od, off)
     # the out-of-place comparator at the same digit width
@@ -437,6 +446,7 @@ def run_segmented(a):
         "oop": {"value": round(oval, 3), "ms_per_step": round(oms, 3), "checked": ook,
                 "extra_bytes": n * 8 + need_o, "extra_frac": round((n * 8 + need_o) / (n * 8), 4)},
         "radsort_over_oop": round(res[best]["value"] / oval, 4),
+        "low_memory": low,
     }), flush=True)
 
 

@@ -285,14 +285,18 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
  * has long segments on a device) that start after the work already on
  * `stream` and that `stream` waits for, each with its own part of the
  * workspace.  workspace: at least radsort_segmented_workspace_size() bytes,
- * or NULL to allocate stream-ordered; with 8-bit digits a caller workspace
- * of at least radsort_segmented_workspace_size_min() bytes that is smaller
- * than that selects the low-memory plan: the segments up to 2^18 elements
- * longer than 16448 are then sorted in place by Radsort itself on one CTA
- * each (Alg. 4-7 on blocks of 32 elements, with 2 sigma + 2 scratch blocks
- * per CTA, two CTAs per SM), the shorter ones out of place in those scratch
- * blocks; on 20,000 lognormal arrays this holds 3.9% of the arrays' bytes
- * instead of 9% and runs about 30% slower.  With a caller workspace the call
+ * or NULL to allocate stream-ordered.  With 8-bit digits a smaller caller
+ * workspace, down to radsort_segmented_workspace_size_min() bytes, selects
+ * the fastest of two low-memory plans that fits: (1) the medium segments
+ * longer than 16448 elements are sorted in place by Radsort itself on one
+ * CTA each (Alg. 4-7 on blocks of 32 elements, with 2 sigma + 2 scratch
+ * blocks per CTA, two CTAs per SM), the shorter ones out of place in those
+ * scratch blocks; (2) as (1), and a long segment whose start is not 16-byte
+ * aligned has its first (at most 3) elements set aside, the rest sorted by
+ * Radsort and those elements merged back, instead of the alternate buffers.
+ * On 20,000 lognormal arrays (2^29 keys + values) the plans hold 9%, 3.9%
+ * and 1.2% of the arrays' bytes; (1) runs about 25% and (2) about 50% slower
+ * than the fastest plan.  With a caller workspace the call
  * issues only kernel launches, memsets and event records / waits, so it can
  * be captured in a CUDA graph (make a first call with long segments before
  * capturing, so that the streams exist).  Calls from several host threads

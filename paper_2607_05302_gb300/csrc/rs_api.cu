@@ -924,6 +924,10 @@ bool seg_aligned(size_t off, int kb, bool hasv)
     return (off * kb) % 16 == 0 && (!hasv || (off * 4) % 16 == 0);
 }
 
+// elements from a segment's start to the next element whose key and value
+// start 16-byte aligned
+size_t seg_head(size_t off) { return (4 - off % 4) % 4; }
+
 // Long segments run on up to SEG_STREAMS internal streams forked from the
 // caller's stream, so that several of them share the SMs (a segment of 2^19
 // elements fills a third of them); each stream has its own workspace slice.
@@ -942,14 +946,18 @@ struct SegPlan {
     size_t large = 0;   // workspace of one long-segment stream
     size_t total = 0;   // base + nstr * large
     uint32_t med_max = 0, med_ctas = 0;
-    bool ip = false;    // the low-memory plan: medium segments in place
+    bool ip = false;    // medium segments in place (level >= 1)
+    int level = 0;      // see seg_plan
     int nstr = 0;       // internal streams used (0: no long segment)
 };
 
 // oop: long segments sorted out of place (Alg. 1) into the caller's
 // alternate arrays, so a stream's slice holds only the comparator's scratch;
-// lowmem: medium segments sorted in place (Radsort per CTA; 8-bit digits)
-radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, bool oop, bool lowmem,
+// level (8-bit digits, not oop): 0 the fastest plan; 1 medium segments
+// sorted in place (Radsort per CTA); 2 as 1, and long segments with an
+// unaligned start sorted in place too (their first elements merged back)
+// instead of out of place
+radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, int db, bool oop, int level,
                         SegPlan *sp)
 {
     size_t large = 0, nlong = 0, nmed = 0;
@@ -978,6 +986,13 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
             if (make_geom(len, kb, hasv, db, &pl, &g) != RADSORT_OK)
                 return RADSORT_EINVAL;
             need = layout(g, nullptr, nullptr);
+        } else if (level >= 2 && db == 8) { // Radsort on the aligned body, the head merged back
+            const size_t h = seg_head(offh[s]), nbody = len - h;
+            const radsort_plan pl = large_plan(nbody);
+            Geom g;
+            if (make_geom(nbody, kb, hasv, db, &pl, &g) != RADSORT_OK)
+                return RADSORT_EINVAL;
+            need = (layout(g, nullptr, nullptr) + 255) / 256 * 256 + head_merge_bytes(nbody, kb, hasv);
         } else { // out of place, Alg. 1, with alternate buffers in the workspace
             need = (len * kb + 255) / 256 * 256 + (hasv ? (len * 4 + 255) / 256 * 256 : 0) +
                    lsd_oop_scratch_bytes(len, kb, db, hasv) + 256;
@@ -986,7 +1001,8 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
             large = (need + 255) / 256 * 256;
     }
     sp->med_max = med_max;
-    sp->ip = lowmem && !oop && db == 8;
+    sp->ip = level >= 1 && !oop && db == 8;
+    sp->level = sp->ip ? level : 0;
     sp->med_ctas = !med_max ? 0
                    : sp->ip ? static_cast<uint32_t>(nmed < seg_ip_ctas() ? nmed : seg_ip_ctas())
                             : seg_med_ctas(med_max, kb, hasv,
@@ -1110,7 +1126,7 @@ radsort_status radsort_segmented_workspace_size(const uint64_t *offsets_host, si
         (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
         return RADSORT_EINVAL;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, false, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, 0, &sp);
     *bytes = s == RADSORT_OK ? sp.total : 0;
     return s;
 }
@@ -1122,11 +1138,15 @@ radsort_status radsort_segmented_workspace_size_min(const uint64_t *offsets_host
     if (!bytes || (key_bytes != 4 && key_bytes != 8) || (value_bytes != 0 && value_bytes != 4) ||
         (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
         return RADSORT_EINVAL;
-    SegPlan fast, lo;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, false, &fast);
-    if (s == RADSORT_OK)
-        s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, true, &lo);
-    *bytes = s == RADSORT_OK ? (lo.total < fast.total ? lo.total : fast.total) : 0;
+    size_t best = 0;
+    radsort_status s = RADSORT_OK;
+    for (int level = 0; level <= 2 && s == RADSORT_OK; ++level) {
+        SegPlan sp;
+        s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, false, level, &sp);
+        if (s == RADSORT_OK && (level == 0 || sp.total < best))
+            best = sp.total;
+    }
+    *bytes = s == RADSORT_OK ? best : 0;
     return s;
 }
 
@@ -1145,11 +1165,12 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
         return RADSORT_EINVAL;
     const bool hasv = values != nullptr;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, false, &sp);
-    if (s == RADSORT_OK && workspace && workspace_bytes < sp.total && digit_bits == 8) {
-        // a caller workspace below the fast plan: the low-memory plan if it fits
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, 0, &sp);
+    // a caller workspace below the fastest plan: the fastest one that fits
+    for (int level = 1; s == RADSORT_OK && workspace && workspace_bytes < sp.total && digit_bits == 8 && level <= 2;
+         ++level) {
         SegPlan lo;
-        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, true, &lo);
+        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, false, level, &lo);
         if (s == RADSORT_OK && workspace_bytes >= lo.total)
             sp = lo;
     }
@@ -1175,6 +1196,21 @@ radsort_status radsort_sort_segmented(void *keys, uint32_t *values, const uint64
                               return sort_common(sk, sv, len, key_bytes, digit_bits, 0, &pl, lw, sp.large, ls,
                                                  -1, nullptr, nullptr);
                           }
+                          if (sp.level >= 2) { // low memory: the head set aside, the aligned body by Radsort
+                              const size_t h = seg_head(off), nbody = len - h;
+                              const size_t hmb = head_merge_bytes(nbody, key_bytes, hasv);
+                              char *mb = lw + sp.large - hmb;
+                              radsort_status r = cuda_status(launch_head_save(sk, sv, static_cast<uint32_t>(h),
+                                                                              key_bytes, mb, ls));
+                              const radsort_plan pl = large_plan(nbody);
+                              if (r == RADSORT_OK)
+                                  r = sort_common(sk + h * key_bytes, hasv ? sv + h : nullptr, nbody, key_bytes,
+                                                  digit_bits, 0, &pl, lw, sp.large - hmb, ls, -1, nullptr, nullptr);
+                              if (r == RADSORT_OK)
+                                  r = cuda_status(launch_head_merge(sk, sv, static_cast<uint32_t>(h), nbody,
+                                                                    key_bytes, mb, ls));
+                              return r;
+                          }
                           char *ak = lw;
                           char *av = ak + (len * key_bytes + 255) / 256 * 256;
                           char *sc = av + (hasv ? (len * 4 + 255) / 256 * 256 : 0);
@@ -1198,7 +1234,7 @@ radsort_status radsort_lsd_oop_segmented_workspace_size(const uint64_t *offsets_
         (digit_bits != 8 && digit_bits != 11) || (num_segments && !offsets_host))
         return RADSORT_EINVAL;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, true, false, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, value_bytes == 4, digit_bits, true, 0, &sp);
     *bytes = s == RADSORT_OK ? sp.total : 0;
     return s;
 }
@@ -1217,9 +1253,9 @@ radsort_status radsort_segmented_autotune(const void *keys, const uint32_t *valu
     const bool hasv = values != nullptr;
     const size_t n = offsets_host[num_segments] - offsets_host[0];
     SegPlan s8, s11;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 8, false, false, &s8);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 8, false, 0, &s8);
     if (s == RADSORT_OK)
-        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 11, false, false, &s11);
+        s = seg_plan(offsets_host, num_segments, key_bytes, hasv, 11, false, 0, &s11);
     if (s != RADSORT_OK)
         return s;
     const size_t end = offsets_host[num_segments];
@@ -1293,7 +1329,7 @@ radsort_status radsort_lsd_oop_sort_segmented(void *keys, uint32_t *values, void
         return RADSORT_EINVAL;
     const bool hasv = values != nullptr;
     SegPlan sp;
-    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, true, false, &sp);
+    radsort_status s = seg_plan(offsets_host, num_segments, key_bytes, hasv, digit_bits, true, 0, &sp);
     if (s != RADSORT_OK)
         return s;
     cudaStream_t st = as_stream(stream);

@@ -113,6 +113,11 @@ constexpr uint32_t SEG_MED = 1u << 18;
 uint32_t seg_small_max(int db);
 uint32_t seg_med_ctas(uint32_t med_max, int kb, bool hasv, size_t budget);
 uint32_t seg_ip_ctas();
+// a long segment with an unaligned start, in the low-memory plan: its first
+// h < 4 elements set aside (save), the rest sorted, then merged back
+size_t head_merge_bytes(size_t nbody, int kb, bool hasv);
+cudaError_t launch_head_save(const void *keys, const uint32_t *vals, uint32_t h, int kb, void *buf, cudaStream_t st);
+cudaError_t launch_head_merge(void *keys, uint32_t *vals, uint32_t h, size_t nbody, int kb, void *buf, cudaStream_t st);
 size_t seg_scratch_bytes(int kb, bool hasv, size_t nseg, uint32_t med_max, uint32_t med_ctas, bool ip);
 cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long long *off_dev,
                              size_t nseg, int kb, int db, uint32_t med_max, uint32_t med_ctas, bool ip,

@@ -846,6 +846,128 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
     }
 }
 
+// ---- a long segment whose start is not 16-byte aligned (low-memory plan) --
+//
+// Its first h < 4 elements (the head) are set aside and sorted, the rest
+// (the body, which starts aligned) is sorted by Radsort, and the head is
+// merged back.  A head element goes before the body's equal keys (it came
+// first), so body element i moves to i + (head keys <= its key) and head
+// element k to k + (body keys < its key).  Every body element moves left by
+// h at most: a chunk of the body is read whole before it is written, and the
+// h elements at its end, whose places the next chunk writes, are read from
+// copies taken before the merge.  A head element is written by the chunk
+// that reads the element it replaces.
+constexpr uint32_t HM_CH = 4096; // body elements per chunk
+constexpr size_t HM_HDR = 128;   // head keys at 0, values at 32, places at 64
+
+template <typename KT> __global__ void k_head_save(const KT *k, const uint32_t *v, uint32_t h, unsigned char *buf)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    KT *hk = reinterpret_cast<KT *>(buf);
+    uint32_t *hv = reinterpret_cast<uint32_t *>(buf + 32);
+    for (uint32_t i = 0; i < h; ++i) { // stable insertion sort of at most 3 elements
+        const KT key = k[i];
+        const uint32_t val = v ? v[i] : 0u;
+        uint32_t j = i;
+        for (; j > 0 && hk[j - 1] > key; --j) {
+            hk[j] = hk[j - 1];
+            hv[j] = hv[j - 1];
+        }
+        hk[j] = key;
+        hv[j] = val;
+    }
+}
+
+// the head's places (binary search in the sorted body) and the copies of the
+// last h elements of every chunk but the last
+template <typename KT>
+__global__ void k_head_prep(const KT *k, const uint32_t *v, uint32_t h, unsigned long long nbody, unsigned char *buf)
+{
+    const KT *hk = reinterpret_cast<const KT *>(buf);
+    unsigned long long *hpos = reinterpret_cast<unsigned long long *>(buf + 64);
+    const unsigned long long nch = (nbody + HM_CH - 1) / HM_CH;
+    KT *bk = reinterpret_cast<KT *>(buf + HM_HDR);
+    uint32_t *bv = reinterpret_cast<uint32_t *>(buf + HM_HDR + (nch * 3 * sizeof(KT) + 15) / 16 * 16);
+    const unsigned long long gid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (gid < h) {
+        const KT key = hk[gid];
+        unsigned long long lo = 0, hi = nbody; // body keys below key: [0, lo)
+        while (lo < hi) {
+            const unsigned long long mid = (lo + hi) / 2;
+            if (k[h + mid] < key)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        hpos[gid] = gid + lo;
+    }
+    for (unsigned long long x = gid; x < (nch - 1) * h; x += stride) {
+        const unsigned long long c = x / h, j = x % h, e = (c + 1) * HM_CH;
+        bk[c * 3 + j] = k[e + j]; // body element e - h + j
+        if (v)
+            bv[c * 3 + j] = v[e + j];
+    }
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(SEG_T) k_head_merge(KT *k, uint32_t *v, uint32_t h, unsigned long long nbody,
+                                                     const unsigned char *buf)
+{
+    constexpr int IT = HM_CH / SEG_T;
+    const KT *hkp = reinterpret_cast<const KT *>(buf);
+    const uint32_t *hvp = reinterpret_cast<const uint32_t *>(buf + 32);
+    const unsigned long long *hpos = reinterpret_cast<const unsigned long long *>(buf + 64);
+    const unsigned long long nch = (nbody + HM_CH - 1) / HM_CH;
+    const KT *bk = reinterpret_cast<const KT *>(buf + HM_HDR);
+    const uint32_t *bv = reinterpret_cast<const uint32_t *>(buf + HM_HDR + (nch * 3 * sizeof(KT) + 15) / 16 * 16);
+    KT hk[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        hk[q] = uint32_t(q) < h ? hkp[q] : KT(0);
+    for (unsigned long long c = blockIdx.x; c < nch; c += gridDim.x) {
+        const unsigned long long s0 = c * HM_CH, e = min(s0 + HM_CH, nbody);
+        const unsigned long long tail = c + 1 < nch ? e - h : e; // from here on: the copies
+        KT key[IT];
+        uint32_t val[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const unsigned long long i = s0 + uint32_t(it * SEG_T + threadIdx.x);
+            key[it] = KT(0);
+            val[it] = 0u;
+            if (i < e) {
+                key[it] = i >= tail ? bk[c * 3 + (i - tail)] : k[h + i];
+                if (v)
+                    val[it] = i >= tail ? bv[c * 3 + (i - tail)] : v[h + i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const unsigned long long i = s0 + uint32_t(it * SEG_T + threadIdx.x);
+            if (i < e) {
+                uint32_t le = 0;
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    le += (uint32_t(q) < h && hk[q] <= key[it]) ? 1u : 0u;
+                k[i + le] = key[it];
+                if (v)
+                    v[i + le] = val[it];
+            }
+        }
+        if (threadIdx.x < h) {
+            const unsigned long long p = hpos[threadIdx.x];
+            const unsigned long long owner = p < h ? 0ull : (p - h) / HM_CH;
+            if (owner == c) {
+                k[p] = hkp[threadIdx.x];
+                if (v)
+                    v[p] = hvp[threadIdx.x];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 } // namespace
 
 // ---------------------------------------------------------------- host side
@@ -980,6 +1102,44 @@ cudaError_t launch_segmented(void *keys, uint32_t *vals, const unsigned long lon
     if (db == 8)
         return vals ? SegImpl<u64, true, 8>::launch(a, st, mc) : SegImpl<u64, false, 8>::launch(a, st, mc);
     return vals ? SegImpl<u64, true, 11>::launch(a, st, mc) : SegImpl<u64, false, 11>::launch(a, st, mc);
+}
+
+size_t head_merge_bytes(size_t nbody, int kb, bool hasv)
+{
+    const size_t nch = (nbody + HM_CH - 1) / HM_CH;
+    const size_t b = HM_HDR + (nch * 3 * kb + 15) / 16 * 16 + (hasv ? nch * 3 * 4 : 0);
+    return (b + 255) / 256 * 256;
+}
+
+cudaError_t launch_head_save(const void *keys, const uint32_t *vals, uint32_t h, int kb, void *buf, cudaStream_t st)
+{
+    unsigned char *b = static_cast<unsigned char *>(buf);
+    if (kb == 4)
+        k_head_save<uint32_t><<<1, 32, 0, st>>>(static_cast<const uint32_t *>(keys), vals, h, b);
+    else
+        k_head_save<unsigned long long><<<1, 32, 0, st>>>(static_cast<const unsigned long long *>(keys), vals, h, b);
+    g_launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_head_merge(void *keys, uint32_t *vals, uint32_t h, size_t nbody, int kb, void *buf, cudaStream_t st)
+{
+    unsigned char *b = static_cast<unsigned char *>(buf);
+    const size_t nch = (nbody + HM_CH - 1) / HM_CH;
+    int grid = num_sms() * 2;
+    if (size_t(grid) > nch)
+        grid = static_cast<int>(nch);
+    const int pgrid = static_cast<int>(((nch - 1) * h + 255) / 256) + 1;
+    if (kb == 4) {
+        k_head_prep<uint32_t><<<pgrid, 256, 0, st>>>(static_cast<const uint32_t *>(keys), vals, h, nbody, b);
+        k_head_merge<uint32_t><<<grid, SEG_T, 0, st>>>(static_cast<uint32_t *>(keys), vals, h, nbody, b);
+    } else {
+        using u64 = unsigned long long;
+        k_head_prep<u64><<<pgrid, 256, 0, st>>>(static_cast<const u64 *>(keys), vals, h, nbody, b);
+        k_head_merge<u64><<<grid, SEG_T, 0, st>>>(static_cast<u64 *>(keys), vals, h, nbody, b);
+    }
+    g_launches += 2;
+    return cudaGetLastError();
 }
 
 } // namespace rs

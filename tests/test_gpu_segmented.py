@@ -124,6 +124,39 @@ def test_low_memory_plan_mixed_and_u64_keys_only():
         assert np.array_equal(got[a:b], ek)
 
 
+@pytest.mark.parametrize("head", [1, 2, 3])
+@pytest.mark.parametrize("kind", ["few", "uniform", "u64"])
+def test_low_memory_plan_unaligned_long_segment(head, kind):
+    """A long segment whose start is `head` elements short of a 16-byte
+    boundary, in the low-memory plan: its first elements are set aside, the
+    aligned rest is sorted by Radsort and they are merged back, each before
+    the equal keys that followed it.  Three distinct keys make nearly every
+    element a tie; bit-exact against the oracle."""
+    lens = [4 - head, 300001, 5]
+    n = sum(lens)
+    off = offsets_of(lens)
+    if kind == "u64":
+        keys = W.make_keys("uniform", n, 64)
+        keys[::3] = keys[4]  # the head's key among the ties
+    else:
+        keys = W.make_keys("uniform", n)
+        if kind == "few":
+            keys = (keys % np.uint32(3)) * np.uint32(0x01010101)
+    need = R.segmented_workspace_size(off, keys.itemsize, 4, 8, minimal=True)
+    assert need < R.segmented_workspace_size(off, keys.itemsize, 4, 8)
+    kt, vt, _ = run_segmented(keys, lens, 8, minimal=True)
+    if kind == "u64":
+        got_k, got_v = kt.cpu().numpy().view(np.uint64), vt.cpu().numpy().view(np.uint32)
+        for s_ in range(len(lens)):
+            a, b = int(off[s_]), int(off[s_ + 1])
+            ek, ev = oracle.lsd_oop(keys[a:b], np.arange(a, b, dtype=np.uint32), n_t=8, sigma=256, bits=8)
+            assert np.array_equal(got_k[a:b], ek) and np.array_equal(got_v[a:b], ev)
+    else:
+        ek, ev = oracle_segmented_u32(keys, lens, 8)
+        assert np.array_equal(kt.cpu().numpy().view(np.uint32), ek)
+        assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
+
+
 @pytest.mark.parametrize("digit_bits", [8, 11])
 def test_segmented_u64_vs_oracle(digit_bits):
     lens = [5, 4096, 2049, 300000, 77777, 1 << 18, (1 << 18) + 2, 1]
