@@ -931,7 +931,9 @@ size_t seg_head(size_t off) { return (4 - off % 4) % 4; }
 // Long segments run on up to SEG_STREAMS internal streams forked from the
 // caller's stream, so that several of them share the SMs (a segment of 2^19
 // elements fills a third of them); each stream has its own workspace slice.
-constexpr int SEG_STREAMS = 4;
+constexpr int SEG_STREAMS = 8;
+// streams used by the plans whose long-segment slices hold alternate arrays
+constexpr int SEG_STREAMS_ALT = 4;
 // the medium pass's scratch (one out-of-place buffer per CTA) is held to
 // this share of the arrays' bytes by running fewer CTAs (at least 16).
 // Measured on 20,000 lognormal arrays (2^29 keys + values, the longest
@@ -1009,7 +1011,8 @@ radsort_status seg_plan(const uint64_t *offh, size_t nseg, int kb, bool hasv, in
                                            static_cast<size_t>(SEG_MED_SHARE * double(n) * (kb + (hasv ? 4 : 0))));
     sp->base = (seg_scratch_bytes(kb, hasv, nseg, med_max, sp->med_ctas, sp->ip) + 255) / 256 * 256;
     sp->large = large;
-    sp->nstr = static_cast<int>(nlong < size_t(SEG_STREAMS) ? nlong : size_t(SEG_STREAMS));
+    const size_t smax = sp->level >= 2 ? size_t(SEG_STREAMS) : size_t(SEG_STREAMS_ALT);
+    sp->nstr = static_cast<int>(nlong < smax ? nlong : smax);
     sp->total = sp->base + size_t(sp->nstr) * large;
     return RADSORT_OK;
 }
