@@ -295,7 +295,7 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
  * aligned has its first (at most 3) elements set aside, the rest sorted by
  * Radsort and those elements merged back, instead of the alternate buffers.
  * On 20,000 lognormal arrays (2^29 keys + values) the plans hold 9%, 3.9%
- * and 1.2% of the arrays' bytes; (1) runs about 25% and (2) about 50% slower
+ * and 1.4% of the arrays' bytes; (1) runs about 20% and (2) about 35% slower
  * than the fastest plan.  With a caller workspace the call
  * issues only kernel launches, memsets and event records / waits, so it can
  * be captured in a CUDA graph (make a first call with long segments before
