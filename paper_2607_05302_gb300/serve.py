@@ -243,6 +243,10 @@ def run_bench(steps=300, cap_bytes=CAP_BYTES, max_streams=512, tight_cap=None):
     """Both methods on the same seeded request stream with the same policy;
     one JSON-ready dict.  tight_cap (bytes): the same stream again under a
     cap small enough that admission, not the GPU, decides concurrency."""
+    # untimed: a short run of each method first (library set-up, stream
+    # creation and the allocator's pools would otherwise fall on the first)
+    for m in ("radsort", "oop"):
+        serve(make_requests(16), m, cap_bytes, max_streams=max_streams)
     reqs_r = make_requests(steps)
     reqs_o = make_requests(steps)
     rs = serve(reqs_r, "radsort", cap_bytes, max_streams=max_streams)
