@@ -48,7 +48,7 @@ FALLBACK_HBM = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="radsort", choices=["radsort", "reference"])
     ap.add_argument("--log2n", type=int, default=30)
@@ -474,7 +474,7 @@ def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream, layo
     wsb = R.radsort_workspace_size(n, kb, 4, db, 0, 0, layout)
     ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=dev)
     free_b = torch.cuda.mem_get_info(dev)[0]
-    nbuf = int(max(2, min(steps + warmup, (free_b * 0.4) // (n * E))))
+    nbuf = int(max(2, min(max(steps, warmup), (free_b * 0.8) // (n * E))))
     kbufs = [torch.empty_like(keys0) for _ in range(nbuf)]
     vbufs = [torch.empty_like(vals0) for _ in range(nbuf)]
 
@@ -493,10 +493,9 @@ def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream, layo
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for s in range(steps):
-            i = warmup + s
-            if i >= nbuf and s > 0:
-                refill(i % nbuf)
-            fn(i % nbuf)
+            if s >= nbuf:  # fewer copies than steps: refill in the timed region
+                refill(s % nbuf)
+            fn(s % nbuf)
         e1.record(stream)
         barrier()
         R.radsort_device_status()
@@ -508,7 +507,7 @@ def time_workload(R, W, dev, log2n, kb, db, steps, warmup, barrier, stream, layo
     R.radsort_trace_enable(False)
     recs = R.radsort_trace_read()
     # the last step's result: sorted and a stable permutation of the input
-    last = (warmup + steps - 1) % nbuf
+    last = (steps - 1) % nbuf
     k = kbufs[last].to(torch.int64) & 0xFFFFFFFF if kb == 4 else kbufs[last] ^ (-(2 ** 63))
     v = vbufs[last].to(torch.int64) & 0xFFFFFFFF
     eq = kbufs[last][1:] == kbufs[last][:-1]
@@ -617,7 +616,9 @@ def main():
 
     free_b = torch.cuda.mem_get_info(dev)[0]
     per_step = n * E
-    nbuf = int(min(a.warmup + a.steps, max(1, (free_b * 0.5) // per_step)))
+    # one fresh copy per timed step where memory allows (at 2^30 u32 + u32,
+    # 24 copies of 8 GiB), so that no copy is refilled inside the timed region
+    nbuf = int(min(max(a.warmup, a.steps), max(1, (free_b * 0.85) // per_step)))
     kbufs = [torch.empty_like(keys0) for _ in range(nbuf)]
     vbufs = [torch.empty_like(vals0) for _ in range(nbuf)]
 
@@ -653,10 +654,9 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for s in range(a.steps):
-        i = a.warmup + s
-        if i >= nbuf and s > 0:  # not enough memory for fresh copies: refill in the timed region
-            refill(i % nbuf)
-        step(i)
+        if s >= nbuf:  # not enough memory for a copy per step: refill in the timed region
+            refill(s % nbuf)
+        step(s)
     ev1.record(stream)
     barrier()
     R.radsort_trace_enable(False)
@@ -735,10 +735,9 @@ def main():
         o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         o0.record(stream)
         for s in range(a.steps):
-            i = a.warmup + s
-            if i >= nbuf and s > 0:
-                refill(i % nbuf)
-            oop_step(i)
+            if s >= nbuf:
+                refill(s % nbuf)
+            oop_step(s)
         o1.record(stream)
         barrier()
         R.radsort_device_status()
