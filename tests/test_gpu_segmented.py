@@ -256,11 +256,14 @@ def test_out_of_place_comparator_vs_oracle(lengths):
     assert np.array_equal(vt.cpu().numpy().view(np.uint32), ev)
 
 
-def test_captured_graph_with_long_segments():
+@pytest.mark.parametrize("minimal", [False, True])
+def test_captured_graph_with_long_segments(minimal):
     """The call with long segments captured in a CUDA graph (fork and join
     over the library's streams inside the capture) and replayed twice on
-    fresh copies gives the oracle's result each time."""
-    lens = LONG_SET
+    fresh copies gives the oracle's result each time; with the smallest
+    workspace too (medium segments in place, unaligned long ones with their
+    first elements merged back)."""
+    lens = LONG_SET + ([3, 40000, 70001] if minimal else [])
     off = offsets_of(lens)
     n = int(off[-1])
     keys = W.make_keys("uniform", n)
@@ -268,7 +271,10 @@ def test_captured_graph_with_long_segments():
     kt, vt = k0.clone(), torch.arange(n, dtype=torch.int32, device=DEV)
     v0 = vt.clone()
     od = torch.from_numpy(off.view(np.int64)).to(DEV)
-    ws = torch.empty(R.segmented_workspace_size(off, 4, 4), dtype=torch.uint8, device=DEV)
+    need = R.segmented_workspace_size(off, 4, 4, minimal=minimal)
+    if minimal:
+        assert need < R.segmented_workspace_size(off, 4, 4)
+    ws = torch.empty(need, dtype=torch.uint8, device=DEV)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
