@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (2^28 u32, 2^30 u64 with 8- and 11-bit digits)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--segments", type=int, default=20000,
+                    help="segmented workload: number of arrays (a smaller batch for profiling)")
     ap.add_argument("--workload", default="radsort", choices=["radsort", "segmented", "serve"],
                     help="radsort: the headline line; segmented: 20,000 lognormal arrays in one "
                          "call under a CUDA graph; serve: the request loop (see serve.py)")
@@ -367,7 +369,7 @@ def run_segmented(a):
     from paper_2607_05302_gb300 import workloads as W
 
     dev = torch.device("cuda", 0)
-    lens = W.lognormal_lengths(20000)
+    lens = W.lognormal_lengths(a.segments)
     off = np.zeros(lens.size + 1, np.uint64)
     np.cumsum(lens.astype(np.uint64), out=off[1:])
     n = int(off[-1])
@@ -436,11 +438,11 @@ def run_segmented(a):
                                                                 workspace=wso))
     oval = n / (oms / 1e3) / 1e9
     print(json.dumps({
-        "metric": "Gkeys/s, batched segmented sort (20,000 arrays, one graph replay)",
+        "metric": f"Gkeys/s, batched segmented sort ({lens.size:,} arrays, one graph replay)",
         "value": round(res[best]["value"], 3), "unit": "Gkeys/s", "n_gpus": 1, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": res[best]["ms_per_step"], "higher_is_better": True,
         "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "segmented_20000_lognormal_median4096_sigma2_u32_index", "n": n,
+        "config": {"workload": f"segmented_{lens.size}_lognormal_median4096_sigma2_u32_index", "n": n,
                    "segments": int(lens.size), "digit_bits": best,
                    "extra_bytes": res[best]["workspace_bytes"],
                    "extra_frac": round(res[best]["workspace_bytes"] / (n * 8), 4),
