@@ -209,31 +209,43 @@ __global__ void __launch_bounds__(SEG_T) k_seg_small(SegArgs a)
     }
 }
 
+// element copies global -> shared memory that complete asynchronously (4 or 8
+// bytes: the segments start at any element)
+template <int BYTES> __device__ __forceinline__ void cp_async_elem(void *smem, const void *gmem)
+{
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // medium segments: out-of-place LSD between the segment and this CTA's
-// scratch region (Alg. 1 per digit), tile by tile
+// scratch region (Alg. 1 per digit), tile by tile.  Every digit's counts come
+// from one read of the segment; the next tile is copied into the second
+// buffer while the current one is ranked and stored.
 template <typename KT, bool HASV, int DB, int TILE>
-__global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
+__global__ void __launch_bounds__(SEG_T, 2) k_seg_medium(SegArgs a)
 {
     using TP = TilePass<KT, HASV, DB, TILE / (32 * SEG_NW)>;
-    constexpr int SIGMA = 1 << DB;
+    constexpr int SIGMA = 1 << DB, NTD = (8 * int(sizeof(KT)) + DB - 1) / DB, LIT = TILE / SEG_T;
     extern __shared__ __align__(16) unsigned char sm[];
-    KT *tk0 = reinterpret_cast<KT *>(sm);
-    KT *tk1 = tk0 + TILE;
-    uint32_t *tv0 = reinterpret_cast<uint32_t *>(tk1 + TILE);
-    uint32_t *tv1 = tv0 + (HASV ? TILE : 0);
-    uint32_t *tcnt = tv1 + (HASV ? TILE : 0);
+    KT *tkb = reinterpret_cast<KT *>(sm); // two tile buffers
+    uint32_t *tvb = reinterpret_cast<uint32_t *>(tkb + 2 * TILE);
+    uint32_t *tcnt = tvb + (HASV ? 2 * TILE : 0);
     uint32_t *bstart = tcnt + SIGMA;
-    unsigned long long *run = reinterpret_cast<unsigned long long *>(bstart + SIGMA);
-    uint32_t *gh = reinterpret_cast<uint32_t *>(run + SIGMA);
-    unsigned char *scratch = reinterpret_cast<unsigned char *>(gh + SIGMA);
+    uint32_t *run = bstart + SIGMA;
+    uint32_t *gh = run + SIGMA; // NTD x SIGMA
+    unsigned char *scratch = reinterpret_cast<unsigned char *>(gh + NTD * SIGMA);
     __shared__ uint32_t s_t;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     KT *keys = static_cast<KT *>(a.keys);
     KT *sck = static_cast<KT *>(a.scr_k) + size_t(blockIdx.x) * a.med_stride;
     uint32_t *scv = HASV ? a.scr_v + size_t(blockIdx.x) * a.med_stride : nullptr;
     const uint32_t count = a.ctr[1];
     const uint32_t mask = SIGMA - 1;
     for (;;) {
-        if (threadIdx.x == 0)
+        __syncthreads(); // every thread has read s_t and finished the last segment
+        if (tid == 0)
             s_t = atomicAdd(&a.ctr[3], 1u);
         __syncthreads();
         const uint32_t t = s_t;
@@ -241,55 +253,85 @@ __global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
             break;
         const uint32_t sgi = a.med_list[t];
         const unsigned long long o = a.off[sgi];
-        const uint32_t len = static_cast<uint32_t>(a.off[sgi + 1] - o);
-        if (len > a.med_stride) { // the host sized the scratch from its offsets
-            set_status(ST_INTERNAL);
+        const unsigned long long len64 = a.off[sgi + 1] - o;
+        if (len64 > a.med_stride) { // the host sized the scratch from its offsets
+            if (tid == 0)
+                set_status(ST_INTERNAL);
             continue;
         }
+        const uint32_t len = static_cast<uint32_t>(len64);
+        // every digit's counts in one pass: the multiset is the same in every round
+        for (int i = tid; i < NTD * SIGMA; i += SEG_T)
+            gh[i] = 0;
+        __syncthreads();
+        for (uint32_t i = tid; i < len; i += SEG_T) {
+            const KT k = keys[o + i];
+#pragma unroll
+            for (int r = 0; r < NTD; ++r)
+                if (r < a.nt)
+                    atomicAdd(&gh[r * SIGMA + digit_of(k, uint32_t(r * DB), mask)], 1u);
+        }
+        __syncthreads();
         KT *sk = keys + o, *dk = sck;
         uint32_t *svp = HASV ? a.vals + o : nullptr, *dvp = scv;
+        const uint32_t ntile = (len + TILE - 1) / TILE;
         for (int r = 0; r < a.nt; ++r) {
             const uint32_t shift = uint32_t(r * DB);
-            // histogram of digit r over the segment (Alg. 1), then its prefix
-            for (int c = threadIdx.x; c < SIGMA; c += SEG_T)
-                gh[c] = 0;
-            __syncthreads();
-            for (uint32_t i = threadIdx.x; i < len; i += SEG_T)
-                atomicAdd(&gh[digit_of(sk[i], shift, mask)], 1u);
-            __syncthreads();
-            if (threadIdx.x < 32) {
-                unsigned long long carry = 0;
+            if (warp == 0) { // bucket starts: exclusive prefix of the round's counts
+                uint32_t carry = 0;
                 for (int c0 = 0; c0 < SIGMA; c0 += 32) {
-                    const unsigned long long v = gh[c0 + threadIdx.x];
-                    const unsigned long long inc = warp_incl_scan(v);
-                    run[c0 + threadIdx.x] = carry + inc - v;
+                    const uint32_t v = gh[r * SIGMA + c0 + lane];
+                    const uint32_t inc = warp_incl_scan(v);
+                    run[c0 + lane] = carry + inc - v;
                     carry += __shfl_sync(0xffffffffu, inc, 31);
                 }
             }
-            __syncthreads();
-            // stable scatter tile by tile
-            for (uint32_t t0 = 0; t0 < len; t0 += TILE) {
-                const uint32_t cnt = min(uint32_t(TILE), len - t0);
-                for (uint32_t i = threadIdx.x; i < cnt; i += SEG_T) {
-                    tk0[i] = sk[t0 + i];
-                    if (HASV)
-                        tv0[i] = svp[t0 + i];
+            auto issue = [&](uint32_t ti) { // tile ti into buffer ti & 1
+                const uint32_t t0 = ti * TILE, cnt = min(uint32_t(TILE), len - t0);
+                KT *bk = tkb + (ti & 1) * TILE;
+                uint32_t *bv = tvb + (ti & 1) * TILE;
+#pragma unroll
+                for (int it = 0; it < LIT; ++it) {
+                    const uint32_t i = it * SEG_T + tid;
+                    if (i < cnt) {
+                        cp_async_elem<sizeof(KT)>(bk + i, sk + t0 + i);
+                        if (HASV)
+                            cp_async_elem<4>(bv + i, svp + t0 + i);
+                    }
                 }
-                __syncthreads();
-                TP::run(tk0, tv0, tk1, tv1, cnt, shift, scratch, tcnt, bstart);
-                for (uint32_t i = threadIdx.x; i < cnt; i += SEG_T) {
-                    const KT kk = tk1[i];
+                cp_async_commit();
+            };
+            issue(0);
+            for (uint32_t ti = 0; ti < ntile; ++ti) {
+                const uint32_t t0 = ti * TILE, cnt = min(uint32_t(TILE), len - t0);
+                KT *tk = tkb + (ti & 1) * TILE;
+                uint32_t *tv = tvb + (ti & 1) * TILE;
+                cp_async_wait_all();
+                __syncthreads(); // the tile is in place; the other buffer is free
+                if (ti + 1 < ntile)
+                    issue(ti + 1);
+                TP::run(tk, tv, tk, tv, cnt, shift, scratch, tcnt, bstart);
+#pragma unroll
+                for (int it = 0; it < LIT; ++it) {
+                    const uint32_t i = it * SEG_T + tid;
+                    if (i >= cnt)
+                        continue;
+                    const KT kk = tk[i];
                     const uint32_t d = digit_of(kk, shift, mask);
-                    const unsigned long long dst = run[d] + (i - bstart[d]);
+                    const uint32_t dst = run[d] + (i - bstart[d]);
+                    if (dst >= len) { // only inconsistent counts get here
+                        set_status(ST_INTERNAL);
+                        continue;
+                    }
                     dk[dst] = kk;
                     if (HASV)
-                        dvp[dst] = tv1[i];
+                        dvp[dst] = tv[i];
                 }
                 __syncthreads();
-                for (int c = threadIdx.x; c < SIGMA; c += SEG_T)
+                for (int c = tid; c < SIGMA; c += SEG_T)
                     run[c] += tcnt[c];
-                __syncthreads();
             }
+            __syncthreads(); // the round's stores precede the next round's copies
             KT *tkp = sk;
             sk = dk;
             dk = tkp;
@@ -298,13 +340,12 @@ __global__ void __launch_bounds__(SEG_T) k_seg_medium(SegArgs a)
             dvp = tvp;
         }
         if (sk != keys + o) { // odd number of passes: the result is in the scratch
-            for (uint32_t i = threadIdx.x; i < len; i += SEG_T) {
+            for (uint32_t i = tid; i < len; i += SEG_T) {
                 keys[o + i] = sk[i];
                 if (HASV)
                     a.vals[o + i] = svp[i];
             }
         }
-        __syncthreads();
     }
 }
 
@@ -983,8 +1024,9 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
     }
     static size_t med_smem()
     {
-        return 2 * TILE * sizeof(KT) + (HASV ? 2 * TILE * 4 : 0) + 2 * SIGMA * 4 + SIGMA * 8 +
-               SIGMA * 4 + TPm::SCRATCH;
+        constexpr int NTD = (8 * int(sizeof(KT)) + DB - 1) / DB;
+        return 2 * TILE * sizeof(KT) + (HASV ? 2 * TILE * 4 : 0) + 3 * SIGMA * 4 + size_t(NTD) * SIGMA * 4 +
+               TPm::SCRATCH;
     }
     // the in-place medium pass (8-bit digits): 4096-element tiles for 4-byte
     // keys, 2048 for 8-byte ones, so that two CTAs fit on an SM
