@@ -276,8 +276,9 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
  * kernels); offsets_host the same values on the host (used to plan the long
  * segments).  Segments up to 4096 elements (2048 for 11-bit digits) are sorted
  * in shared memory.  Segments up to 2^18 elements are sorted out of place in
- * per-CTA scratch as long as the longest of them (2 CTAs per SM), the paper's
- * suggestion of reusing T as the A' of Alg. 1 for short arrays (Sec. 5).
+ * per-CTA scratch as long as the longest of them (at most 2 CTAs per SM, held
+ * to 6% of the arrays' bytes), the paper's suggestion of reusing T as the A'
+ * of Alg. 1 for short arrays (Sec. 5).
  * Both classes are handled by one persistent launch each.  Longer segments
  * run the full Radsort (Alg. 2), or Alg. 1 with alternate buffers in the
  * workspace when their start is not 16-byte aligned; they are spread, longest
@@ -295,7 +296,7 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
  * aligned has its first (at most 3) elements set aside, the rest sorted by
  * Radsort and those elements merged back, instead of the alternate buffers.
  * On 20,000 lognormal arrays (2^29 keys + values) the plans hold 9%, 3.9%
- * and 1.4% of the arrays' bytes; (1) runs about 20% and (2) about 35% slower
+ * and 1.4% of the arrays' bytes; (1) runs about 25% and (2) about 40% slower
  * than the fastest plan.  With a caller workspace the call
  * issues only kernel launches, memsets and event records / waits, so it can
  * be captured in a CUDA graph (make a first call with long segments before
