@@ -384,15 +384,17 @@ template <typename KT, bool HASV, int TILE> struct IpCfg {
     static constexpr int SIGMA = 256;
     static constexpr int NTD = int(sizeof(KT)) * 8 / 8;
     using TP = TilePass<KT, HASV, 8, TILE / (32 * SEG_NW)>;
-    static constexpr size_t O_TV = size_t(TILE) * sizeof(KT);
-    static constexpr size_t O_CNT = O_TV + (HASV ? size_t(TILE) * 4 : 0);
+    // two tile buffers of keys, then two of values: the next tile is copied
+    // while the current one is ranked
+    static constexpr size_t O_TV = size_t(2) * TILE * sizeof(KT);
+    static constexpr size_t O_CNT = O_TV + (HASV ? size_t(2) * TILE * 4 : 0);
     static constexpr size_t O_GH = O_CNT + size_t(3) * SIGMA * 4; // tcnt, bstart, run
     static constexpr size_t O_MAP = O_GH + size_t(NTD) * SIGMA * 4;
     static constexpr size_t O_RING = O_MAP + size_t(2) * IP_NB * 2;
     static constexpr size_t O_SCR = (O_RING + size_t(IP_FCAP) * 2 + 15) / 16 * 16;
     static constexpr size_t SMEM = O_SCR + TP::SCRATCH;
     // Finalize reuses the tile buffer: the free scratch blocks and the cut list
-    static_assert(size_t(TILE) * sizeof(KT) >= 1600 + IP_NB, "tile buffer holds the Finalize lists");
+    static_assert(size_t(2) * TILE * sizeof(KT) >= 1600 + IP_NB, "tile buffers hold the Finalize lists");
     static_assert(TP::SCRATCH >= size_t(SEG_NW) * 2 * IP_K * 4, "scratch holds the move lists");
 };
 
@@ -403,8 +405,8 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
     constexpr int SIGMA = C::SIGMA, DB = 8, LIT = TILE / SEG_T;
     constexpr uint32_t IP_HELD = 0xFFFFFFFFu, IP_TAILDST = 0xFFFFFFFEu;
     extern __shared__ __align__(16) unsigned char sm[];
-    KT *tk = reinterpret_cast<KT *>(sm);
-    uint32_t *tv = reinterpret_cast<uint32_t *>(sm + C::O_TV);
+    KT *tkb = reinterpret_cast<KT *>(sm);
+    uint32_t *tvb = reinterpret_cast<uint32_t *>(sm + C::O_TV);
     uint32_t *tcnt = reinterpret_cast<uint32_t *>(sm + C::O_CNT);
     uint32_t *bstart = tcnt + SIGMA;
     uint32_t *run = bstart + SIGMA;
@@ -486,21 +488,34 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
             // and the scratch, which serves as A' of Alg. 1
             KT *sk = Ak, *dk = Tk;
             uint32_t *sv = Av, *dv = Tv;
+            const uint32_t ntile = (m + TILE - 1) / TILE;
             for (int r = 0; r < C::NTD; ++r) {
                 const uint32_t shift = uint32_t(r * DB);
                 starts(r);
-                for (uint32_t t0 = 0; t0 < m; t0 += TILE) {
-                    const uint32_t cnt = min(uint32_t(TILE), m - t0);
+                auto issue = [&](uint32_t ti) { // tile ti into buffer ti & 1
+                    const uint32_t t0 = ti * TILE, cnt = min(uint32_t(TILE), m - t0);
+                    KT *bk = tkb + (ti & 1) * TILE;
+                    uint32_t *bv = tvb + (ti & 1) * TILE;
 #pragma unroll
                     for (int it = 0; it < LIT; ++it) {
                         const uint32_t i = it * SEG_T + tid;
                         if (i < cnt) {
-                            tk[i] = sk[t0 + i];
+                            cp_async_elem<sizeof(KT)>(bk + i, sk + t0 + i);
                             if (HASV)
-                                tv[i] = sv[t0 + i];
+                                cp_async_elem<4>(bv + i, sv + t0 + i);
                         }
                     }
-                    __syncthreads();
+                    cp_async_commit();
+                };
+                issue(0);
+                for (uint32_t ti = 0; ti < ntile; ++ti) {
+                    const uint32_t t0 = ti * TILE, cnt = min(uint32_t(TILE), m - t0);
+                    KT *tk = tkb + (ti & 1) * TILE;
+                    uint32_t *tv = tvb + (ti & 1) * TILE;
+                    cp_async_wait_all();
+                    __syncthreads(); // the tile is in place; the other buffer is free
+                    if (ti + 1 < ntile)
+                        issue(ti + 1);
                     C::TP::run(tk, tv, tk, tv, cnt, shift, scratch, tcnt, bstart);
 #pragma unroll
                     for (int it = 0; it < LIT; ++it) {
@@ -521,8 +536,8 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
                     __syncthreads();
                     for (int c = tid; c < SIGMA; c += SEG_T)
                         run[c] += tcnt[c];
-                    __syncthreads();
                 }
+                __syncthreads(); // the round's stores precede the next round's copies
                 KT *xk = sk;
                 sk = dk;
                 dk = xk;
@@ -543,37 +558,55 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
             starts(r);
             for (uint32_t j = tid; j < nb; j += SEG_T)
                 pin[j] = IP_NONE;
-            __syncthreads();
-            for (uint32_t t0 = 0; t0 < m; t0 += TILE) {
-                const uint32_t cnt = min(uint32_t(TILE), m - t0);
-                const uint32_t ft = s_ft;
-                // the tile, read through the block map (the first round's map
-                // is the identity: the segment in place)
-                if (r == 0) {
+            // tile ti into buffer ti & 1, read through the block map (the
+            // first round's map is the identity: the segment in place); the
+            // next tile's blocks are not on the free list yet, so nothing
+            // stores into them while they are copied
+            auto issue = [&](uint32_t ti) {
+                const uint32_t t0 = ti * TILE, cnt = min(uint32_t(TILE), m - t0);
+                KT *bk = tkb + (ti & 1) * TILE;
+                uint32_t *bv = tvb + (ti & 1) * TILE;
 #pragma unroll
-                    for (int it = 0; it < LIT; ++it) {
-                        const uint32_t i = it * SEG_T + tid;
-                        if (i < cnt) {
-                            tk[i] = Ak[t0 + i];
-                            if (HASV)
-                                tv[i] = Av[t0 + i];
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int it = 0; it < LIT; ++it) {
-                        const uint32_t i = it * SEG_T + tid;
-                        if (i < cnt) {
-                            const uint32_t e = t0 + i, ph = pi[e >> IP_LB], w = e & (IP_B - 1);
-                            const bool ok = ph < nphys; // else a broken map, reported
-                            if (!ok)
+                for (int it = 0; it < LIT; ++it) {
+                    const uint32_t i = it * SEG_T + tid;
+                    if (i < cnt) {
+                        const uint32_t e = t0 + i;
+                        const KT *srck;
+                        const uint32_t *srcv;
+                        if (r == 0) {
+                            srck = Ak + e;
+                            srcv = HASV ? Av + e : nullptr;
+                        } else {
+                            const uint32_t ph = pi[e >> IP_LB], w = e & (IP_B - 1);
+                            if (ph >= nphys) { // a broken map, reported
                                 set_status(ST_INTERNAL);
-                            tk[i] = ok ? koff(ph)[w] : KT(0);
-                            if (HASV)
-                                tv[i] = ok ? voff(ph)[w] : 0u;
+                                bk[i] = KT(0);
+                                if (HASV)
+                                    bv[i] = 0u;
+                                continue;
+                            }
+                            srck = koff(ph) + w;
+                            srcv = HASV ? voff(ph) + w : nullptr;
                         }
+                        cp_async_elem<sizeof(KT)>(bk + i, srck);
+                        if (HASV)
+                            cp_async_elem<4>(bv + i, srcv);
                     }
                 }
+                cp_async_commit();
+            };
+            __syncthreads(); // pin cleared, starts written, the last round's stores done
+            const uint32_t ntile = (m + TILE - 1) / TILE;
+            issue(0);
+            for (uint32_t ti = 0; ti < ntile; ++ti) {
+                const uint32_t t0 = ti * TILE, cnt = min(uint32_t(TILE), m - t0);
+                KT *tk = tkb + (ti & 1) * TILE;
+                uint32_t *tv = tvb + (ti & 1) * TILE;
+                const uint32_t ft = s_ft;
+                cp_async_wait_all();
+                __syncthreads(); // the tile is in place; the other buffer is free
+                if (ti + 1 < ntile)
+                    issue(ti + 1);
                 // its blocks are free now (the partial block in place is never
                 // reused: it is shorter than a block)
                 const uint32_t q0 = t0 >> IP_LB, nq = ((t0 + cnt - 1) >> IP_LB) - q0 + 1;
@@ -651,8 +684,8 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
                 __syncthreads();
                 for (int c = tid; c < SIGMA; c += SEG_T)
                     run[c] += tcnt[c];
-                __syncthreads();
             }
+            __syncthreads(); // the round's stores precede the next round's copies
             uint16_t *x = pi;
             pi = pin;
             pin = x;
@@ -662,7 +695,7 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium_ip(SegArgs a)
         // The tile buffer holds the free scratch blocks, their use flags and
         // the cycles left uncut.
         uint16_t *occ = pin;
-        uint16_t *freeT = reinterpret_cast<uint16_t *>(sm);
+        uint16_t *freeT = reinterpret_cast<uint16_t *>(sm); // the tile buffers are free now
         unsigned char *usedT = sm + 1040;
         uint16_t *flist = reinterpret_cast<uint16_t *>(sm + 1600);
         for (uint32_t p = tid; p < nb; p += SEG_T)
@@ -1028,9 +1061,9 @@ template <typename KT, bool HASV, int DB> struct SegImpl {
         return 2 * TILE * sizeof(KT) + (HASV ? 2 * TILE * 4 : 0) + 3 * SIGMA * 4 + size_t(NTD) * SIGMA * 4 +
                TPm::SCRATCH;
     }
-    // the in-place medium pass (8-bit digits): 4096-element tiles for 4-byte
-    // keys, 2048 for 8-byte ones, so that two CTAs fit on an SM
-    static constexpr int IP_TILE = sizeof(KT) == 4 ? 4096 : 2048;
+    // the in-place medium pass (8-bit digits): two buffers of 2048-element
+    // tiles for 4-byte keys, 1024 for 8-byte ones, so that two CTAs fit on an SM
+    static constexpr int IP_TILE = sizeof(KT) == 4 ? 2048 : 1024;
     using IC = IpCfg<KT, HASV, IP_TILE>;
     static cudaError_t launch(const SegArgs &a, cudaStream_t st, int med_ctas)
     {
