@@ -291,13 +291,14 @@ radsort_status radsort_lsd_oop_scratch_size(size_t n, int key_bytes, int value_b
  * the fastest of two low-memory plans that fits: (1) the medium segments
  * longer than 16448 elements are sorted in place by Radsort itself on one
  * CTA each (Alg. 4-7 on blocks of 32 elements, with 2 sigma + 2 scratch
- * blocks per CTA, two CTAs per SM), the shorter ones out of place in those
+ * blocks per CTA, two CTAs per SM, one per SM on 7/8 of the SMs beside long
+ * segments), the shorter ones out of place in those
  * scratch blocks; (2) as (1), and a long segment whose start is not 16-byte
  * aligned has its first (at most 3) elements set aside, the rest sorted by
  * Radsort and those elements merged back, instead of the alternate buffers.
- * On 20,000 lognormal arrays (2^29 keys + values) the plans hold 9%, 3.9%
- * and 1.4% of the arrays' bytes; (1) runs about 25% and (2) about 40% slower
- * than the fastest plan.  With a caller workspace the call
+ * On 20,000 lognormal arrays (2^29 keys + values) the plans hold 9%, 3.4%
+ * and 0.95% of the arrays' bytes; (1) and (2) run about 30% slower than the
+ * fastest plan.  With a caller workspace the call
  * issues only kernel launches, memsets and event records / waits, so it can
  * be captured in a CUDA graph (make a first call with long segments before
  * capturing, so that the streams exist).  Calls from several host threads
