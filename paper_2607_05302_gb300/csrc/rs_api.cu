@@ -195,8 +195,14 @@ static void auto_plan_chunks(size_t n, int kb, int vb, int db, radsort_plan *pl)
 // plan asks for it.  Larger blocks are faster (fewer list entries and bulk
 // copies per tile, fewer blocks to permute in Finalize) but the scratch array
 // grows with b, so the plan takes the largest block size whose workspace is
-// within 2% of the array's bytes, or within 1.25x the least workspace of any
-// block size when no block size meets 2%.
+// within 2% of the array's bytes, 1.25x the least workspace of any block
+// size, or 4 MiB above that least as long as that stays within a quarter of
+// the array's bytes (below about 2^26 elements no block size meets 2%: the
+// look-back ring and tables alone take ~2 MB; a quarter keeps the footprint
+// well below an out-of-place sort's).
+// Measured (u32 keys + values, us a sort): 2^20 b = 256 309, 512 259;
+// 2^22 506, 390; 2^24 1231, 820; 2^25 2233, 1398 -- blocks of 256 leave many
+// list entries per tile.
 static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
 {
     if (pl->layout != RADSORT_LAYOUT_CHUNKS && n < (size_t(1) << 31)) {
@@ -212,7 +218,8 @@ static void auto_plan(size_t n, int kb, int vb, int db, radsort_plan *pl)
                 least = ws[i];
         }
         const double two = 0.02 * double(n) * double(kb + vb);
-        const double budget = two > 1.25 * double(least) ? two : 1.25 * double(least);
+        const double some = std::min(double(least) + double(4u << 20), 0.25 * double(n) * double(kb + vb));
+        const double budget = std::max({two, 1.25 * double(least), some});
         uint32_t best_b = 0;
         for (int i = 0; i < 5; ++i)
             if (ws[i] && double(ws[i]) <= budget)
