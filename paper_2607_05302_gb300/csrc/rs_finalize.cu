@@ -204,6 +204,45 @@ __global__ void k_fz_jump(unsigned long long *jump, uint32_t npi, int mode, uint
         atomicAdd(&changes[round], 1u);
 }
 
+// The same pointer jumping for a small permutation (n_pi <= FZ_SMALL_NPI):
+// one CTA with the entries in shared memory, steps until one changes
+// nothing (windows at least double each step, so 33 steps bound it), in one
+// launch instead of one per (JUMP_STEPS + 1)-fold growth.
+constexpr uint32_t FZ_SMALL_NPI = 12288;
+
+__global__ void __launch_bounds__(1024) k_fz_jump_small(unsigned long long *jump, uint32_t npi, int mode)
+{
+    extern __shared__ unsigned long long sj[];
+    for (uint32_t x = threadIdx.x; x < npi; x += blockDim.x)
+        sj[x] = jump[x];
+    __syncthreads();
+    for (int step = 0; step < 34; ++step) {
+        bool changed = false;
+        for (uint32_t x = threadIdx.x; x < npi; x += blockDim.x) {
+            const unsigned long long e = sj[x];
+            const uint32_t v = hi32(e);
+            if (v == ABS)
+                continue;
+            const uint32_t nx = lo32(e);
+            if (nx >= npi)
+                continue; // only a broken entry points out of the permutation
+            const unsigned long long f = sj[nx];
+            const uint32_t fv = hi32(f);
+            if (fv == ABS)
+                continue;
+            const unsigned long long ne = pk(lo32(f), mode == 0 ? min(v, fv) : v + fv);
+            if (ne != e) {
+                sj[x] = ne;
+                changed = true;
+            }
+        }
+        if (!__syncthreads_or(changed))
+            break;
+    }
+    for (uint32_t x = threadIdx.x; x < npi; x += blockDim.x)
+        jump[x] = sj[x];
+}
+
 // classify each moving block in pi's top bits: moving / on a cycle / the
 // cycle's minimum position
 __global__ void k_fz_classify(FinArgs a)
@@ -923,16 +962,30 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     for (unsigned long long w = JUMP_STEPS + 1; w < g.npi; w *= JUMP_STEPS + 1)
         ++rounds;
     rounds += 1;
+    static DeviceOnce jattr;
+    const cudaError_t ej = jattr.run([] {
+        return cudaFuncSetAttribute(k_fz_jump_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(FZ_SMALL_NPI * 8));
+    });
+    if (ej != cudaSuccess)
+        return ej;
+    const bool small = g.npi <= FZ_SMALL_NPI;
     k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
     k_fz_edges<<<grid, FIN_T, 0, st>>>(a);
     uint32_t *chg = a.ctr + C_WORDS; // per-round change counters (cleared with the flags)
-    for (int r = 0; r < rounds; ++r)
-        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 0, chg, r);
+    if (small)
+        k_fz_jump_small<<<1, 1024, size_t(g.npi) * 8, st>>>(a.jump, g.npi, 0);
+    else
+        for (int r = 0; r < rounds; ++r)
+            k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 0, chg, r);
     k_fz_classify<<<grid, FIN_T, 0, st>>>(a);
     k_fz_reset<<<grid, FIN_T, 0, st>>>(a.jump, g.npi);
     k_fz_rank_edges<<<grid, FIN_T, 0, st>>>(a);
-    for (int r = 0; r < rounds; ++r)
-        k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 1, chg + 64, r);
+    if (small)
+        k_fz_jump_small<<<1, 1024, size_t(g.npi) * 8, st>>>(a.jump, g.npi, 1);
+    else
+        for (int r = 0; r < rounds; ++r)
+            k_fz_jump<<<grid, FIN_T, 0, st>>>(a.jump, g.npi, 1, chg + 64, r);
     k_fz_chains<<<grid, FIN_T, 0, st>>>(a);
     k_fz_order<<<grid, FIN_T, 0, st>>>(a);
     const size_t bbytes = size_t(g.b) * (g.kb + (g.hasv ? 4 : 0));
@@ -962,7 +1015,7 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
         const uint32_t tail = static_cast<uint32_t>(g.n - size_t(g.nA) * g.b);
         if (tail)
             k_fz_tail<KT><<<(tail + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, tail);
-        g_launches += 10 + 2 * rounds;
+        g_launches += 10 + 2 * (small ? 1 : rounds);
         return cudaGetLastError();
     }
     uint4 *wplan = reinterpret_cast<uint4 *>(base + L.wplan);
@@ -970,7 +1023,7 @@ cudaError_t fin_impl(const Geom &g, const Bufs &w, uint32_t *pi, unsigned long l
     k_fz_winplan<<<(L.nwin + FIN_T - 1) / FIN_T, FIN_T, 0, st>>>(a, wplan, wsegs);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fz_compact<KT>, FIN_T, csm);
     k_fz_compact<KT><<<sms * (per_sm > 0 ? per_sm : 1), FIN_T, csm, st>>>(a, wplan, wsegs);
-    g_launches += 11 + 2 * rounds;
+    g_launches += 11 + 2 * (small ? 1 : rounds);
     return cudaGetLastError();
 }
 
