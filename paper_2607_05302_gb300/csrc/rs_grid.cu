@@ -351,7 +351,7 @@ template <int DB>
 __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint32_t n, uint32_t lb,
                                                      uint32_t H, uint32_t nA, uint32_t npi,
                                                      const uint32_t *pi, uint32_t *pin,
-                                                     uint32_t *tab, uint32_t *state)
+                                                     uint32_t *tab, uint32_t *state, uint32_t clear)
 {
     constexpr int SIGMA = 1 << DB;
     // s_a: scan buffer; s_list: bucket of the k-th bucket start strictly
@@ -360,6 +360,9 @@ __global__ void __launch_bounds__(1024) k_grid_prep(const uint32_t *hist_r, uint
     __shared__ int s_skip;
     const uint32_t b = 1u << lb;
     auto bar = [] { __syncthreads(); };
+    // a small map is cleared here rather than by a memset launch
+    for (uint32_t i = threadIdx.x; i < clear; i += blockDim.x)
+        pin[H + i] = 0xFFFFFFFFu;
     if (threadIdx.x == 0)
         s_skip = 0;
     __syncthreads();
@@ -1449,16 +1452,21 @@ cudaError_t launch_grid_prep(const Geom &g, const Bufs &w, const uint32_t *pi, u
                              int round, cudaStream_t st)
 {
     const uint32_t NB = static_cast<uint32_t>((g.n + g.b - 1) / g.b);
-    cudaError_t e = cudaMemsetAsync(pin + g.H, 0xFF, size_t(NB) * 4, st);
-    if (e != cudaSuccess)
-        return e;
+    // the new map's data entries start unset: cleared by the prep kernel
+    // itself when there are few of them, else by a memset
+    const uint32_t clear = NB <= 65536 ? NB : 0u;
+    if (!clear) {
+        cudaError_t e = cudaMemsetAsync(pin + g.H, 0xFF, size_t(NB) * 4, st);
+        if (e != cudaSuccess)
+            return e;
+    }
     const uint32_t n = static_cast<uint32_t>(g.n);
     if (g.db == 8)
         k_grid_prep<8><<<1, 1024, 0, st>>>(w.hist + size_t(round) * g.sigma, n, g.lb, g.H, g.nA, g.npi,
-                                           pi, pin, w.tab, w.state);
+                                           pi, pin, w.tab, w.state, clear);
     else
         k_grid_prep<11><<<1, 1024, 0, st>>>(w.hist + size_t(round) * g.sigma, n, g.lb, g.H, g.nA,
-                                            g.npi, pi, pin, w.tab, w.state);
+                                            g.npi, pi, pin, w.tab, w.state, clear);
     g_launches += 1;
     return cudaGetLastError();
 }
