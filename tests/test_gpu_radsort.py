@@ -81,6 +81,20 @@ def test_logical_sequence_each_round(plan):
         assert np.array_equal(from_dev(ov, np.uint32), lv)
 
 
+@pytest.mark.parametrize("n", [64 * 11263 + 17, 64 * 11264 + 5])
+def test_finalize_small_and_large_pointer_jumping(n):
+    """Grid layout, blocks of 64: n_pi = n/64 + 1025 is 12288 (the largest
+    map that Finalize pointer-jumps in one CTA in shared memory) or 12289
+    (the multi-launch path); both against the oracle, with ties."""
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    keys[::9] = keys[4]
+    vals = W.index_payload(n)
+    gk, gv = gpu_sort(keys, vals, block_size=64, num_chunks=0, layout="grid")
+    ek, ev = oracle_sort(keys, vals, 32, 8)
+    assert np.array_equal(gk, ek) and np.array_equal(gv, ev)
+
+
 @pytest.mark.parametrize("layout", ["chunks", "grid", "scratch"])
 @pytest.mark.parametrize("dist", W.DISTRIBUTIONS)
 def test_config1_distributions(dist, layout):
