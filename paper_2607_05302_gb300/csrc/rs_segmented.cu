@@ -357,8 +357,9 @@ __global__ void __launch_bounds__(SEG_T, 2) k_seg_medium(SegArgs a)
 // nfull + IP_S - 1).  Before the first round the map is the identity and the
 // segment's partial last block lies in place (IP_TAIL).  A round (Alg. 5 on
 // one processor, with the output on the block grid of the grid layout) reads
-// the sequence tile by tile; a tile's blocks go to the free list once it is
-// in shared memory; the tile is ranked stably by the round's digit; every
+// the sequence tile by tile (the next tile copied while the current one is
+// ranked); a tile's blocks go to the free list once it is in shared memory;
+// the tile is ranked stably by the round's digit; every
 // output block that the tile is the first to touch takes the next free block;
 // then the tile is stored.  After the last round, Finalize (Alg. 7) moves
 // logical block j to place j along chains, which start at a place that holds
