@@ -685,6 +685,15 @@ def main():
                 "algorithmic_bytes_per_launch": n * 2 * E, "peak_source": src,
                 "avg_launch_ms": round(avg_round, 4)}
     step_bytes = n * (4 * 2 * E) if kb == 4 and db == 8 else None
+    # Finalize moves every element once at most: n * 2E bytes at most, over
+    # its mean duration (a bound on its bandwidth: blocks already in place
+    # are not moved)
+    fin_ms = [t for ph, rd, t in recs if ph == "Finalize"]
+    finalize = None
+    if fin_ms:
+        fm = statistics.mean(fin_ms)
+        finalize = {"ms": round(fm, 4), "bytes": n * 2 * E, "gbs": round(n * 2 * E / (fm / 1e3) / 1e9, 1),
+                    "frac": round(n * 2 * E / (fm / 1e3) / 1e9 / hbm, 4)}
 
     # ---- the paper's chunk layout (Sec. 4.3), one chunk per SM, same data
     plan2 = None
@@ -809,6 +818,7 @@ def main():
             "clocks": clk, "extra_bytes": wsb, "extra_frac": round(wsb / (n * E), 5),
             "oop": oop, "chunk_layout": plan2, "extra": extra, "serve": serve_line,
             "phases_ms": {k: round(statistics.mean(v), 4) for k, v in phases.items()},
+            "finalize": finalize,
             "algorithmic_bytes_per_step": step_bytes,
         }
         print(json.dumps(line), flush=True)
